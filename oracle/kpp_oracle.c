@@ -1,0 +1,378 @@
+/*
+ * kpp_oracle.c -- plain, serial, FP64 CPU oracle for k-means++ D^2 seeding.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the correctness reference that the
+ * CUDA library is checked against.  Only the test suite, the smoke check in
+ * __graft_entry__.py and the CPU-baseline leg of bench.py may load or run it.
+ * It shares no code, header, table or helper with the CUDA path, and the CUDA
+ * path never calls it.
+ *
+ * What it computes (Heydarpour Shahrezaei & Tavoli, "Parallelization of
+ * Kmeans++ using CUDA", arXiv:1908.02136):
+ *   - Algorithm 1 (Serial K-means++): the first seed is a uniformly random
+ *     point; every point's nearest distance starts at infinity; for each new
+ *     seed the distance of every point to that seed is taken, the nearest
+ *     squared distance d_sn is kept, and the next seed is drawn with
+ *     probability P(n_l) = d_sn / sum_w d_sn_w (Algorithm 1, the probability
+ *     line; the upper summation limit is read as N).
+ *   - Section II: the index of every chosen centre is kept in an array and the
+ *     centre coordinates are looked up from the point array by that index.
+ *   - Section II (Thrust reduction): the sum of all D^2 is taken in double.
+ *
+ * Readings where the paper is silent (each is repeated in the design doc):
+ *   R1  The random draw is u_m = Philox4x64-10(key = {seed, stream},
+ *       counter = {m, 0, 0, 0}), word 0 mapped to [0,1) as (w0 >> 11) * 2^-53.
+ *       Philox4x64-10 follows Salmon, Moraes, Dror and Shaw, "Parallel Random
+ *       Numbers: As Easy as 1, 2, 3", SC'11 (round function, multipliers and
+ *       Weyl key increments as published there).
+ *   R2  First seed: i_0 = min(floor(u_0 * N), N - 1).
+ *   R3  Draw of seed m (m >= 1) by inverse CDF in index order: with
+ *       P_i = sum_{k <= i} D^2_k (sequential FP64), T = P_{N-1}, t = u_m * T,
+ *       i_m is the smallest i with P_i > t (strict, so zero-weight points are
+ *       never drawn).  If rounding leaves no P_i > t, i_m is the largest i
+ *       with D^2_i > 0.
+ *   R4  Degenerate data: if T == 0 at a draw (fewer distinct points than K),
+ *       seeding stops; the remaining indices are -1 and the status is
+ *       KPP_ORACLE_DEGENERATE.
+ *   R5  Distances are squared Euclidean, summed over j = 0..d-1 in order, in
+ *       FP64, in the difference form sum_j (x_ij - c_j)^2.  Stored BF16 and
+ *       FP8-e4m3 coordinates are decoded exactly (value = s_i * q_ij for FP8,
+ *       formed in double).
+ *   R6  There are K distance passes and K-1 draws; the D^2 returned is the one
+ *       after the pass for the last centre, and phi = sum_i D^2_i (FP64,
+ *       sequential).
+ *
+ * Quantisers (precision forms; not in the paper):
+ *   BF16  round-to-nearest-even of the FP32 value (IEEE 754 rounding applied
+ *         to the 8-bit-exponent, 7-bit-fraction format).
+ *   FP8   OCP 8-bit floating point, E4M3 ("fn": no infinities, max 448):
+ *         per row s_i = max_j |x_ij| / 448 (FP32 division; s_i = 1 for an
+ *         all-zero row), q_ij = RNE-with-saturation of the FP32 quotient
+ *         x_ij / s_i.
+ *
+ * Build: gcc -O2 -ffp-contract=off -shared -fPIC (no fused multiply-add, so
+ * the arithmetic is the one written here on every host).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define KPP_ORACLE_OK 0
+#define KPP_ORACLE_INVALID 1
+#define KPP_ORACLE_DEGENERATE 5
+
+#define KPP_ORACLE_F32 0
+#define KPP_ORACLE_BF16 1
+#define KPP_ORACLE_FP8_E4M3 2
+
+/* ------------------------------------------------------------------------ */
+/* Philox4x64-10 (Salmon et al., SC'11).                                      */
+/* ------------------------------------------------------------------------ */
+
+static void mul_hi_lo_64(uint64_t a, uint64_t b, uint64_t *hi, uint64_t *lo)
+{
+    /* Schoolbook 64x64 -> 128 with 32-bit halves. */
+    uint64_t a_lo = a & 0xffffffffu, a_hi = a >> 32;
+    uint64_t b_lo = b & 0xffffffffu, b_hi = b >> 32;
+    uint64_t p0 = a_lo * b_lo;
+    uint64_t p1 = a_lo * b_hi;
+    uint64_t p2 = a_hi * b_lo;
+    uint64_t p3 = a_hi * b_hi;
+    uint64_t mid = (p0 >> 32) + (p1 & 0xffffffffu) + (p2 & 0xffffffffu);
+    *lo = (p0 & 0xffffffffu) | (mid << 32);
+    *hi = p3 + (p1 >> 32) + (p2 >> 32) + (mid >> 32);
+}
+
+void kpp_oracle_philox4x64_10(const uint64_t ctr_in[4], const uint64_t key_in[2],
+                              uint64_t out[4])
+{
+    /* Round multipliers and key (Weyl) increments of Philox4x64. */
+    const uint64_t M0 = 0xD2E7470EE14C6C93ull;
+    const uint64_t M1 = 0xCA5A826395121157ull;
+    const uint64_t W0 = 0x9E3779B97F4A7C15ull; /* golden ratio */
+    const uint64_t W1 = 0xBB67AE8584CAA73Bull; /* sqrt(3) - 1 */
+    uint64_t x[4] = {ctr_in[0], ctr_in[1], ctr_in[2], ctr_in[3]};
+    uint64_t k0 = key_in[0], k1 = key_in[1];
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) {
+            k0 += W0;
+            k1 += W1;
+        }
+        uint64_t hi0, lo0, hi1, lo1;
+        mul_hi_lo_64(M0, x[0], &hi0, &lo0);
+        mul_hi_lo_64(M1, x[2], &hi1, &lo1);
+        uint64_t y0 = hi1 ^ x[1] ^ k0;
+        uint64_t y1 = lo1;
+        uint64_t y2 = hi0 ^ x[3] ^ k1;
+        uint64_t y3 = lo0;
+        x[0] = y0;
+        x[1] = y1;
+        x[2] = y2;
+        x[3] = y3;
+    }
+    memcpy(out, x, sizeof(x));
+}
+
+/* Reading R1: u_m in [0, 1) with 53 random bits. */
+double kpp_oracle_uniform(uint64_t seed, uint64_t stream, uint64_t m)
+{
+    uint64_t ctr[4] = {m, 0, 0, 0};
+    uint64_t key[2] = {seed, stream};
+    uint64_t out[4];
+    kpp_oracle_philox4x64_10(ctr, key, out);
+    return (double)(out[0] >> 11) * 0x1.0p-53;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Stored formats.                                                            */
+/* ------------------------------------------------------------------------ */
+
+double kpp_oracle_decode_bf16(uint16_t h)
+{
+    uint32_t bits = (uint32_t)h << 16; /* BF16 is the top half of FP32 */
+    float f;
+    memcpy(&f, &bits, sizeof(f));
+    return (double)f;
+}
+
+double kpp_oracle_decode_e4m3(uint8_t q)
+{
+    int sign = (q >> 7) & 1;
+    int e = (q >> 3) & 0xf;
+    int man = q & 0x7;
+    double v;
+    if (e == 0xf && man == 0x7)
+        return NAN;
+    if (e == 0)
+        v = ldexp((double)man, -9); /* subnormal: man * 2^(1-7) / 8 */
+    else
+        v = ldexp(1.0 + (double)man / 8.0, e - 7);
+    return sign ? -v : v;
+}
+
+uint16_t kpp_oracle_encode_bf16(float f)
+{
+    uint32_t bits;
+    memcpy(&bits, &f, sizeof(bits));
+    if ((bits & 0x7fffffffu) > 0x7f800000u) /* NaN: keep it a quiet NaN */
+        return (uint16_t)((bits >> 16) | 0x0040u);
+    /* Round to nearest, ties to even, on the 16 dropped bits. */
+    uint32_t lsb = (bits >> 16) & 1u;
+    uint32_t rounded = bits + 0x7fffu + lsb;
+    return (uint16_t)(rounded >> 16);
+}
+
+uint8_t kpp_oracle_encode_e4m3_sat(float f)
+{
+    if (isnan(f))
+        return 0x7f;
+    uint8_t sign = signbit(f) ? 0x80 : 0x00;
+    double a = fabs((double)f);
+    if (a >= 448.0)
+        return sign | 0x7e; /* saturate to the largest finite value */
+    if (a < 0x1.0p-6) {
+        /* Subnormal range: quantum 2^-9; a code of 8 is the smallest normal. */
+        double c = rint(a * 512.0); /* default rounding mode: ties to even */
+        return sign | (uint8_t)c;
+    }
+    int ex;
+    frexp(a, &ex);      /* a = f * 2^ex, f in [0.5, 1) */
+    int e = ex - 1;     /* a in [2^e, 2^(e+1)) with e in [-6, 8] */
+    double scaled = rint(ldexp(a, 3 - e)); /* in [8, 16] */
+    if (scaled >= 16.0) {
+        scaled = 8.0;
+        e += 1;
+    }
+    int biased = e + 7;
+    uint8_t code = (uint8_t)((biased << 3) | ((int)scaled - 8));
+    if (code > 0x7e)
+        code = 0x7e;
+    return sign | code;
+}
+
+void kpp_oracle_quantize_bf16(const float *x, int64_t n, uint16_t *out)
+{
+    for (int64_t i = 0; i < n; ++i)
+        out[i] = kpp_oracle_encode_bf16(x[i]);
+}
+
+void kpp_oracle_quantize_fp8(const float *x, int64_t N, int32_t d, uint8_t *q,
+                             float *scales)
+{
+    for (int64_t i = 0; i < N; ++i) {
+        const float *row = x + i * (int64_t)d;
+        float mx = 0.0f;
+        for (int32_t j = 0; j < d; ++j) {
+            float a = fabsf(row[j]);
+            if (a > mx)
+                mx = a;
+        }
+        float s = (mx > 0.0f) ? mx / 448.0f : 1.0f;
+        scales[i] = s;
+        for (int32_t j = 0; j < d; ++j) {
+            volatile float v = row[j] / s; /* the FP32 quotient is what is rounded */
+            q[i * (int64_t)d + j] = kpp_oracle_encode_e4m3_sat(v);
+        }
+    }
+}
+
+/* Decoded value of coordinate j of point i, in double (reading R5). */
+static double coord(const void *pts, const float *scales, int dtype, int64_t i,
+                    int32_t d, int32_t j)
+{
+    int64_t k = i * (int64_t)d + j;
+    switch (dtype) {
+    case KPP_ORACLE_F32:
+        return (double)((const float *)pts)[k];
+    case KPP_ORACLE_BF16:
+        return kpp_oracle_decode_bf16(((const uint16_t *)pts)[k]);
+    default:
+        return (double)scales[i] * kpp_oracle_decode_e4m3(((const uint8_t *)pts)[k]);
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* The draw (reading R3).                                                     */
+/* ------------------------------------------------------------------------ */
+
+/* Inverse-CDF draw over D2[0..N) at uniform u; returns -1 if sum is zero. */
+int64_t kpp_oracle_pick(const double *D2, int64_t N, double u, double *t_out,
+                        double *T_out)
+{
+    double T = 0.0;
+    for (int64_t i = 0; i < N; ++i)
+        T += D2[i];
+    double t = u * T;
+    if (t_out)
+        *t_out = t;
+    if (T_out)
+        *T_out = T;
+    if (T == 0.0)
+        return -1;
+    double P = 0.0;
+    for (int64_t i = 0; i < N; ++i) {
+        P += D2[i];
+        if (P > t)
+            return i;
+    }
+    for (int64_t i = N - 1; i >= 0; --i)
+        if (D2[i] > 0.0)
+            return i;
+    return -1;
+}
+
+/* Per-draw record, used to compare a replayed trajectory with the oracle's own
+ * choices.  For draw m: own = the index the oracle draws from its own D^2;
+ * t, T as in R3; P_before / P_at = the sequential prefix sums just before and
+ * at the replayed index (the one actually taken). */
+typedef struct {
+    int64_t own;
+    double t;
+    double T;
+    double P_before;
+    double P_at;
+} kpp_oracle_draw;
+
+/*
+ * Algorithm 1, with readings R1-R6.
+ *   points     N x d row-major stored values (dtype F32, BF16 or FP8-E4M3)
+ *   scales     FP8 per-row scales [N] (NULL otherwise)
+ *   forced     optional index prefix of length n_forced that replaces the
+ *              oracle's own draws (replay / teacher forcing); NULL if none
+ *   idx_out    [K] chosen indices (-1 after a degenerate stop)
+ *   d2_out     [N] nearest squared distance after the last pass (FP64)
+ *   phi_out    [1] sum of d2_out (FP64), or NULL
+ *   draws_out  [K] per-draw records (entry 0: own = first uniform pick), or NULL
+ *   d2_hist    [K x N] D^2 after each pass, or NULL (tiny cases only)
+ * Returns KPP_ORACLE_OK, KPP_ORACLE_INVALID or KPP_ORACLE_DEGENERATE.
+ */
+int kpp_oracle_seed(const void *points, const float *scales, int dtype, int64_t N,
+                    int32_t d, int32_t K, uint64_t seed, uint64_t stream,
+                    const int64_t *forced, int32_t n_forced, int64_t *idx_out,
+                    double *d2_out, double *phi_out, kpp_oracle_draw *draws_out,
+                    double *d2_hist)
+{
+    if (!points || !idx_out || !d2_out || N < 1 || d < 1 || K < 1 || K > N ||
+        n_forced < 0 || n_forced > K || (n_forced > 0 && !forced) ||
+        dtype < 0 || dtype > 2 || (dtype == KPP_ORACLE_FP8_E4M3 && !scales))
+        return KPP_ORACLE_INVALID;
+    for (int32_t m = 0; m < n_forced; ++m)
+        if (forced[m] < 0 || forced[m] >= N)
+            return KPP_ORACLE_INVALID;
+
+    /* Decode every stored coordinate to double once (reading R5). */
+    double *X = (double *)malloc(sizeof(double) * (size_t)N * (size_t)d);
+    if (!X)
+        return KPP_ORACLE_INVALID;
+    for (int64_t i = 0; i < N; ++i)
+        for (int32_t j = 0; j < d; ++j)
+            X[i * (int64_t)d + j] = coord(points, scales, dtype, i, d, j);
+
+    for (int32_t m = 0; m < K; ++m)
+        idx_out[m] = -1;
+
+    /* First seed, uniformly at random (Algorithm 1; reading R2). */
+    double u0 = kpp_oracle_uniform(seed, stream, 0);
+    int64_t first = (int64_t)floor(u0 * (double)N);
+    if (first > N - 1)
+        first = N - 1;
+    if (draws_out) {
+        memset(draws_out, 0, sizeof(kpp_oracle_draw) * (size_t)K);
+        draws_out[0].own = first;
+    }
+    idx_out[0] = (n_forced > 0) ? forced[0] : first;
+
+    /* O(l) = infinity for every point (Algorithm 1). */
+    for (int64_t i = 0; i < N; ++i)
+        d2_out[i] = INFINITY;
+
+    int status = KPP_ORACLE_OK;
+    for (int32_t m = 0; m < K; ++m) {
+        /* Centre coordinates looked up by index (Section II). */
+        const double *c = X + idx_out[m] * (int64_t)d;
+        /* Distance to the newest seed and nearest squared distance. */
+        for (int64_t i = 0; i < N; ++i) {
+            double delta = 0.0;
+            for (int32_t j = 0; j < d; ++j) {
+                double diff = X[i * (int64_t)d + j] - c[j];
+                delta += diff * diff;
+            }
+            if (delta < d2_out[i])
+                d2_out[i] = delta;
+        }
+        if (d2_hist)
+            memcpy(d2_hist + (size_t)m * (size_t)N, d2_out, sizeof(double) * (size_t)N);
+        if (m == K - 1)
+            break;
+
+        /* Draw of seed m+1 with probability D^2 / sum D^2 (reading R3). */
+        double u = kpp_oracle_uniform(seed, stream, (uint64_t)(m + 1));
+        double t, T;
+        int64_t own = kpp_oracle_pick(d2_out, N, u, &t, &T);
+        if (T == 0.0) { /* reading R4 */
+            status = KPP_ORACLE_DEGENERATE;
+            break;
+        }
+        int64_t taken = (m + 1 < n_forced) ? forced[m + 1] : own;
+        idx_out[m + 1] = taken;
+        if (draws_out) {
+            double P = 0.0;
+            for (int64_t i = 0; i < taken; ++i)
+                P += d2_out[i];
+            draws_out[m + 1].own = own;
+            draws_out[m + 1].t = t;
+            draws_out[m + 1].T = T;
+            draws_out[m + 1].P_before = P;
+            draws_out[m + 1].P_at = P + d2_out[taken];
+        }
+    }
+    if (phi_out) {
+        double phi = 0.0;
+        for (int64_t i = 0; i < N; ++i)
+            phi += d2_out[i];
+        *phi_out = phi;
+    }
+    free(X);
+    return status;
+}
