@@ -1,0 +1,352 @@
+"""Benchmark of GB300 k-means++ D^2 seeding (one JSON line on rank 0).
+
+A step is one whole seeding (all K passes and K-1 draws) of the named
+workload, through the library's C ABI, with the points already resident in
+HBM.  L2 is flushed (a 512 MiB buffer is written) between timed steps, and
+each step is timed with CUDA events on the launching stream.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+                  [--dtype f32|bf16|fp8] [--impl kpp|reference]
+
+Under torchrun (N > 1) every rank seeds its own replica of the workload
+(Philox stream id = rank), with no collective on the data path: weak
+scaling.  Timing is barrier-bracketed and the max over ranks is reported.
+
+``--impl reference`` times the FP64 CPU oracle (the correctness reference,
+not a GPU code) on a bounded sample of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import csv
+import io
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "k-means++ seeding ms & N·K·d/s; HBM GB/s vs peak; BF16/batched vs FP32"
+UNIT = "N*K*d/s"
+DEFAULT_WORKLOAD = "gmm-N1e6-d32-K256"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
+    ap.add_argument("--dtype", default="f32", choices=["f32", "bf16", "fp8"])
+    ap.add_argument("--impl", default="kpp", choices=["kpp", "reference"])
+    ap.add_argument("--form", type=int, default=0)
+    ap.add_argument("--lanes", type=int, default=0)
+    ap.add_argument("--ctas-per-sm", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        rows = [r for r in csv.reader(io.StringIO(out)) if len(r) >= 9]
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in rows:
+            for name, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def cpu_info():
+    model = None
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part")):
+                model = line.split(":", 1)[1].strip()
+                break
+    except OSError:
+        pass
+    return os.cpu_count(), model
+
+
+def time_oracle(points, wl, K_sample, seed, stream_id, scales=None):
+    """The FP64 oracle on the first K_sample passes of the workload."""
+    import oracle
+
+    t0 = time.perf_counter()
+    oracle.seed(points, K_sample, seed, stream_id, scales=scales)
+    return time.perf_counter() - t0
+
+
+def oracle_sample_passes(wl):
+    # about 10-30 s of serial FP64 work at ~1.5 ns per coordinate per pass
+    per_pass = wl.N * wl.d * 1.5e-9
+    return max(1, min(wl.K, int(15.0 / max(per_pass, 1e-9))))
+
+
+def run_reference(args, rank, world):
+    """--impl reference: the FP64 CPU oracle as it stands, on the host cores."""
+    from paper_1908_02136_gb300 import datagen
+
+    if rank != 0:
+        return
+    wl = datagen.WORKLOADS[args.workload]
+    import numpy as np
+
+    import oracle
+
+    x = datagen.workload_points(wl) if wl.N <= 2_000_000 else datagen.gmm(
+        min(wl.N, 2_000_000), wl.d, wl.n_comp, wl.data_seed, wl.mean_box, wl.sigma, wl.weights,
+        wl.outlier_frac)
+    N = x.shape[0]
+    K_s = max(1, oracle_sample_passes(wl) // max(1, args.steps + args.warmup))
+    for _ in range(args.warmup):
+        oracle.seed(x[: min(N, 10_000)], 2, 1)
+    times = []
+    for s in range(args.steps):
+        times.append(time_oracle(x, wl, K_s, wl.draw_seed, s))
+    ms = 1e3 * sum(times) / len(times)
+    value = N * K_s * wl.d / (sum(times) / len(times))
+    cores, model = cpu_info()
+    sample = f"{N} points x {wl.d} dims, {K_s} of {wl.K} passes per step (serial FP64 oracle)"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": wl.name, "N": N, "d": wl.d, "K": wl.K,
+                                        "dtype": "f32", "passes_per_step": K_s},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": sample, "host_cores": cores, "cpu": model},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import numpy as np
+    import torch
+
+    import paper_1908_02136_gb300 as kpp
+    from paper_1908_02136_gb300 import datagen
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+
+    def barrier():
+        if pg is not None:
+            pg.barrier()
+
+    wl = datagen.WORKLOADS[args.workload]
+    x_np = datagen.workload_points(wl) if wl.N <= 2_000_000 else None
+    x = torch.from_numpy(x_np).to(dev) if x_np is not None else datagen.workload_points(wl, dev)
+    N, d, K = wl.N, wl.d, wl.K
+    scales = None
+    if args.dtype == "f32":
+        pts = x
+    elif args.dtype == "bf16":
+        pts = kpp.quantize(x, "bf16")
+    else:
+        pts, scales = kpp.quantize(x, "fp8")
+    eb = {"f32": 4, "bf16": 2, "fp8": 1}[args.dtype]
+    opts = kpp.Options()
+    opts.form = args.form
+    opts.lanes_per_row = args.lanes
+    opts.ctas_per_sm = args.ctas_per_sm
+    code = {"f32": kpp.F32, "bf16": kpp.BF16, "fp8": kpp.FP8_E4M3}[args.dtype]
+    ws = kpp.workspace_for(N, d, K, code, dev, opts)
+    idx = torch.empty(K, dtype=torch.int64, device=dev)
+    d2 = torch.empty(N, dtype=torch.float32, device=dev)
+    phi = torch.empty(1, dtype=torch.float64, device=dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.Stream(dev)
+    sh = __import__("ctypes").c_void_p(stream.cuda_stream)
+    seed = wl.draw_seed
+    stream_id = rank
+
+    def launch():
+        st = kpp.kpp_seed(pts.data_ptr(), None if scales is None else scales.data_ptr(), N, d, K,
+                          code, seed, stream_id, None, 0, idx.data_ptr(), d2.data_ptr(),
+                          phi.data_ptr(), ws.data_ptr(), ws.numel(), sh, opts)
+        if st != kpp.OK:
+            raise kpp.KppError(st, "kpp_seed")
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            flush.fill_(1)
+            launch()
+        st = kpp.kpp_read_status(ws.data_ptr(), sh)
+        if st != kpp.OK:
+            raise kpp.KppError(st, "warmup")
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        torch.cuda.synchronize(dev)
+        barrier()
+        torch.cuda.synchronize(dev)
+        sampler = ClockSampler(local)
+        sampler.start()
+        time.sleep(0.3)  # let the sampler take a first sample
+        for s in range(args.steps):
+            flush.fill_(s & 0xFF)  # L2 flush between steps, outside the events
+            starts[s].record(stream)
+            launch()
+            ends[s].record(stream)
+        torch.cuda.synchronize(dev)
+        clocks = sampler.stop()
+        barrier()
+    step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
+    total_ms = sum(step_ms)
+    if pg is not None:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    nkd = float(N) * K * d
+    value = nkd * world * args.steps / (total_ms / 1e3)
+    # parity of the timed result (cheap invariants; full parity lives in tests/)
+    idx_h = idx.cpu().numpy()
+    assert np.all((idx_h >= 0) & (idx_h < N)) and len(set(idx_h.tolist())) == K
+    assert float(d2[idx].abs().max()) == 0.0
+
+    # e2e: host points (pinned) -> C ABI -> host results, wall clock incl. copies
+    e2e = None
+    if not args.no_e2e:
+        xh = pts.cpu().pin_memory()
+        sh_host = None if scales is None else scales.cpu().pin_memory()
+        bufs = None
+        hidx, hd2, hphi, st, bufs = kpp.seed_host(xh, K, seed, stream_id, dtype=args.dtype,
+                                                  row_scales_host=sh_host, device=dev, opts=opts)
+        e2e_steps = max(1, min(args.steps, 5))
+        torch.cuda.synchronize(dev)
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            hidx, hd2, hphi, st, bufs = kpp.seed_host(xh, K, seed, stream_id, dtype=args.dtype,
+                                                      row_scales_host=sh_host, device=dev,
+                                                      opts=opts, buffers=bufs)
+            if st != kpp.OK:
+                raise kpp.KppError(st, "kpp_seed_host")
+        e2e_s = time.perf_counter() - t0
+        if pg is not None:
+            t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+            pg.all_reduce(t, op=pg.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        h2d = N * d * eb + (4 * N if scales is not None else 0)
+        d2h = 8 * K + 4 * N + 8
+        e2e = {"value": nkd * world * e2e_steps / e2e_s, "unit": UNIT,
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "ms_per_step": 1e3 * e2e_s / e2e_steps}
+
+    # roofline of the dominant kernel (the per-pass streamed kernel)
+    peaks = measured_peaks()
+    peak = peaks["hbm_gbs"] if peaks else 6800.0
+    launches_per_step = K
+    per_launch_ms = ms_per_step / launches_per_step
+    alg_bytes = N * d * eb + (4 * N if scales is not None else 0) + 8 * N
+    achieved = alg_bytes / (per_launch_ms / 1e3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None,
+                "peak_source": "measured" if peaks else "fallback",
+                "algorithmic_bytes_per_launch": alg_bytes,
+                "points_only_frac": (N * d * eb) / (per_launch_ms / 1e3) / 1e9 / peak}
+
+    cpu_baseline = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+
+        stored = x_np if args.dtype == "f32" else (
+            pts.cpu().numpy().view(np.uint16) if args.dtype == "bf16" else pts.cpu().numpy())
+        if stored is None:
+            stored = x.cpu().numpy()
+        K_s = oracle_sample_passes(wl)
+        sc_np = None if scales is None else scales.cpu().numpy()
+        dt_s = time_oracle(stored, wl, K_s, seed, stream_id, sc_np)
+        cores, model = cpu_info()
+        cpu_baseline = {"value": N * K_s * d / dt_s, "unit": UNIT, "cores": 1, "kind": "oracle",
+                        "sample": f"full workload data, first {K_s} of {K} passes "
+                                  f"(serial FP64 oracle, {dt_s:.1f} s)",
+                        "host_cores": cores, "cpu": model}
+
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": args.dtype, "data": "synthetic",
+            "config": {"workload": wl.name, "N": N, "d": d, "K": K, "storage": args.dtype,
+                       "form": "streamed", "parallelism": f"replicas{world}",
+                       "l2": "flushed between steps (512 MiB write)",
+                       "step_ms_min": min(step_ms), "step_ms_max": max(step_ms)},
+            "clocks": clocks, "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
+            "roofline": roofline, "cpu_baseline": cpu_baseline,
+        }), flush=True)
+    if pg is not None:
+        pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,179 @@
+/*
+ * kpp.h -- C ABI of libkpp, GB300 (sm_103a) k-means++ D^2 seeding.
+ *
+ * The method is k-means++ seeding as parallelised in Heydarpour Shahrezaei &
+ * Tavoli, "Parallelization of Kmeans++ using CUDA" (arXiv:1908.02136):
+ *   - Algorithm 1 (serial) / Algorithm 2 (parallel): the first seed is a
+ *     uniformly random point; every point's nearest squared distance D^2
+ *     starts at infinity; after each new seed every point's distance to it is
+ *     taken and D^2 keeps the minimum; the next seed is drawn with probability
+ *     D^2_i / sum_w D^2_w.
+ *   - Section II: chosen seeds are kept as an index array and their
+ *     coordinates are read from the point array by index; the sum of D^2 is
+ *     taken in double precision (the Thrust reduction).
+ * Conventions this library fixes where the paper is silent:
+ *   - draws: u_m = Philox4x64-10(key = {seed, stream_id}, counter = {m,0,0,0}),
+ *     word 0 mapped to [0,1) as (w0 >> 11) * 2^-53 (Salmon et al., SC'11);
+ *   - first seed: i_0 = min(floor(u_0 * N), N - 1);
+ *   - seed m >= 1: inverse CDF in index order, t = u_m * T with T = sum D^2 in
+ *     FP64; i_m is the first index whose FP64 prefix sum exceeds t (strictly),
+ *     so points with D^2 = 0 are never drawn; if rounding leaves none, the
+ *     last point with D^2 > 0 is taken.  Prefix sums are hierarchical
+ *     (per-CTA FP64 block sums, then a rescan of the winning block only).
+ *   - distances are squared Euclidean in the difference form
+ *     sum_j (x_ij - c_j)^2, accumulated in FP32; D^2 is stored in FP32.
+ *   - K distance passes and K-1 draws; phi = sum_i D^2_i in FP64 after the
+ *     last pass.
+ *   - if sum D^2 = 0 at a draw (fewer distinct points than K), seeding stops:
+ *     the remaining indices are -1 and the device status becomes
+ *     KPP_ERR_DEGENERATE.
+ *
+ * Memory and ownership: every buffer is allocated and owned by the caller.
+ * Unless a parameter says "host", pointers are CUDA device pointers on the
+ * current device.  Points are row-major [N x d], contiguous, and the base
+ * must be 16-byte aligned.  No entry point allocates device memory; scratch
+ * lives in the caller's workspace (size from kpp_workspace_size, 256-byte
+ * aligned).  A workspace must not be shared by calls in flight at the same
+ * time.
+ *
+ * Asynchrony and errors: compute entry points enqueue work on `stream` and
+ * return at once.  Argument errors are returned synchronously and nothing is
+ * enqueued.  Errors found on the device (degenerate data, a barrier
+ * timeout) are written to a status word in the workspace; kpp_read_status
+ * synchronises the stream and returns it.  No exception crosses this ABI.
+ */
+#ifndef KPP_H
+#define KPP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define KPP_API __attribute__((visibility("default")))
+#else
+#define KPP_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t; NULL is the legacy default stream. */
+typedef struct CUstream_st *kpp_stream_t;
+
+typedef enum {
+    KPP_OK = 0,
+    KPP_ERR_INVALID_ARG = 1, /* bad size, NULL or misaligned pointer, K > N ... */
+    KPP_ERR_CUDA = 2,        /* a CUDA runtime call failed */
+    KPP_ERR_LAUNCH = 3,      /* a launch was refused (e.g. co-residency) */
+    KPP_ERR_TIMEOUT = 4,     /* a bounded device wait gave up (device status) */
+    KPP_ERR_DEGENERATE = 5,  /* sum D^2 = 0 before K seeds (device status) */
+    KPP_ERR_WORKSPACE = 6,   /* workspace NULL, misaligned or too small */
+    KPP_ERR_UNSUPPORTED = 7  /* option combination not built */
+} kpp_status;
+
+/* Storage type of the points; distances are always accumulated in FP32. */
+typedef enum {
+    KPP_F32 = 0,
+    KPP_BF16 = 1,     /* bfloat16 bit patterns */
+    KPP_FP8_E4M3 = 2  /* OCP E4M3 codes, value = row_scale[i] * decode(q_ij) */
+} kpp_dtype;
+
+typedef enum {
+    KPP_FORM_AUTO = 0,
+    KPP_FORM_STREAMED = 1,   /* one kernel per seed, captured in a CUDA graph */
+    KPP_FORM_PERSISTENT = 2  /* one cooperative launch for all K passes */
+} kpp_form;
+
+/* Tuning knobs; a zeroed struct (or NULL) means "choose automatically". */
+typedef struct {
+    int32_t form;          /* kpp_form */
+    int32_t lanes_per_row; /* lanes that share one point row: 1,2,4,8,16,32 */
+    int32_t ctas_per_sm;   /* resident CTAs per SM the grid is sized for */
+    int32_t use_graph;     /* streamed form: 0/1 = CUDA graph, -1 = plain launches */
+    uint32_t timeout_us;   /* bounded device waits; 0 = 2,000,000 us */
+    int32_t reserved[3];
+} kpp_options;
+
+/* Human-readable name of a status code (static string, never NULL). */
+KPP_API const char *kpp_status_string(kpp_status status);
+
+/* Library version as 10000*major + 100*minor + patch. */
+KPP_API int32_t kpp_version(void);
+
+/*
+ * Bytes of device workspace kpp_seed needs for this problem on the current
+ * device (0 if the arguments are invalid).  The size depends on N, d, dtype,
+ * the options and the device's SM count, not on the data.
+ */
+KPP_API size_t kpp_workspace_size(int64_t N, int32_t d, int32_t K, kpp_dtype dtype,
+                          const kpp_options *opts);
+
+/*
+ * k-means++ seeding of one problem (Algorithm 1 / Algorithm 2).
+ *   points        [N x d] stored values of `dtype`, 16-byte aligned
+ *   row_scales    [N] FP32 per-row scales (KPP_FP8_E4M3 only, else NULL)
+ *   N, d, K       1 <= K <= N < 2^31, 1 <= d <= 4096
+ *   seed, stream_id  Philox key of the draws
+ *   forced_prefix [n_forced] device indices that replace the first n_forced
+ *                 draws (replay / teacher forcing), or NULL with n_forced = 0
+ *   indices_out   [K] int64: chosen seeds in draw order
+ *   d2_out        [N] FP32: nearest squared distance after the last pass
+ *   phi_out       [1] FP64: sum of d2_out, or NULL
+ *   workspace     >= kpp_workspace_size(...) bytes, 256-byte aligned
+ * Returns KPP_OK once the work is enqueued on `stream`; device-side
+ * outcomes are read with kpp_read_status.
+ */
+KPP_API kpp_status kpp_seed(const void *points, const float *row_scales, int64_t N, int32_t d,
+                    int32_t K, kpp_dtype dtype, uint64_t seed, uint64_t stream_id,
+                    const int64_t *forced_prefix, int32_t n_forced,
+                    int64_t *indices_out, float *d2_out, double *phi_out,
+                    void *workspace, size_t workspace_bytes, kpp_stream_t stream,
+                    const kpp_options *opts);
+
+/*
+ * End-to-end seeding from HOST buffers: copies the host points (and scales)
+ * into the caller's device buffers, seeds as kpp_seed, copies indices, D^2
+ * and phi back to the host, and synchronises `stream`.  Pinned host memory
+ * gives asynchronous copies; pageable memory works but is slower.
+ *   host_points   [N x d] host stored values; dev_points: device buffer of
+ *                 the same size (16-byte aligned)
+ *   host_scales / dev_scales   FP8 only, else NULL
+ *   host_indices [K] int64, host_d2 [N] FP32, host_phi [1] FP64 (may be NULL)
+ *   dev_indices [K], dev_d2 [N], dev_phi [1] device buffers
+ * Returns the device status (KPP_OK, KPP_ERR_DEGENERATE, ...) after the sync.
+ */
+KPP_API kpp_status kpp_seed_host(const void *host_points, const float *host_scales,
+                         void *dev_points, float *dev_scales, int64_t N, int32_t d,
+                         int32_t K, kpp_dtype dtype, uint64_t seed, uint64_t stream_id,
+                         int64_t *host_indices, float *host_d2, double *host_phi,
+                         int64_t *dev_indices, float *dev_d2, double *dev_phi,
+                         void *workspace, size_t workspace_bytes, kpp_stream_t stream,
+                         const kpp_options *opts);
+
+/*
+ * Synchronises `stream` and returns the device status word of the last
+ * call that used `workspace`: KPP_OK, KPP_ERR_DEGENERATE or KPP_ERR_TIMEOUT
+ * (KPP_ERR_CUDA if the copy itself fails).
+ */
+KPP_API kpp_status kpp_read_status(const void *workspace, kpp_stream_t stream);
+
+/*
+ * Precision forms (not in the paper): quantise FP32 points once, before
+ * seeding, so each pass reads fewer bytes.
+ *   x [N x d] FP32 device input.
+ *   to = KPP_BF16: out is [N x d] uint16 BF16, round to nearest even;
+ *        row_scales must be NULL.
+ *   to = KPP_FP8_E4M3: out is [N x d] uint8 E4M3 codes and row_scales [N]
+ *        FP32 with s_i = max_j |x_ij| / 448 (1 for an all-zero row) and
+ *        q_ij = round-to-nearest-even, saturating, of the FP32 x_ij / s_i.
+ * Asynchronous on `stream`.
+ */
+KPP_API kpp_status kpp_quantize(const float *x, int64_t N, int32_t d, kpp_dtype to, void *out,
+                        float *row_scales, kpp_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KPP_H */

@@ -1,0 +1,274 @@
+"""GB300-native k-means++ D^2 seeding (arXiv:1908.02136) -- Python binding.
+
+A thin ctypes binding over ``libkpp.so`` (C ABI in ``include/kpp.h``).  Every
+step of the seeding path runs in the library's CUDA kernels; this module
+only marshals arguments.  PyTorch supplies device memory and streams.
+
+Two layers:
+
+* the C entry points under their C names (``kpp_seed``, ``kpp_workspace_size``,
+  ``kpp_read_status``, ``kpp_quantize``, ``kpp_seed_host``,
+  ``kpp_status_string``, ``kpp_version``), taking raw pointers and sizes;
+* tensor helpers (``seed``, ``seed_host``, ``quantize``) that allocate the
+  outputs and the workspace with torch and call the entry points on torch's
+  current stream.
+
+There is no CPU fallback: if the library cannot be built or loaded, import
+of the entry points raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import build as _build
+
+F32, BF16, FP8_E4M3 = 0, 1, 2
+FORM_AUTO, FORM_STREAMED, FORM_PERSISTENT = 0, 1, 2
+(OK, ERR_INVALID_ARG, ERR_CUDA, ERR_LAUNCH, ERR_TIMEOUT, ERR_DEGENERATE,
+ ERR_WORKSPACE, ERR_UNSUPPORTED) = range(8)
+
+_DTYPE_NAMES = {"f32": F32, "fp32": F32, "float32": F32, "bf16": BF16, "bfloat16": BF16,
+                "fp8": FP8_E4M3, "e4m3": FP8_E4M3, "fp8_e4m3": FP8_E4M3}
+
+
+class KppError(RuntimeError):
+    def __init__(self, status: int, where: str = ""):
+        self.status = status
+        super().__init__(f"{where}: {kpp_status_string(status)} (status {status})")
+
+
+class Options(ctypes.Structure):
+    """Mirror of kpp_options."""
+
+    _fields_ = [("form", ctypes.c_int32), ("lanes_per_row", ctypes.c_int32),
+                ("ctas_per_sm", ctypes.c_int32), ("use_graph", ctypes.c_int32),
+                ("timeout_us", ctypes.c_uint32), ("reserved", ctypes.c_int32 * 3)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load_library(build_if_stale: bool = True):
+    """Load libkpp.so (building it in-tree first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.build() if build_if_stale else _build.LIB
+        if not os.path.exists(path):
+            raise ImportError(f"libkpp.so not built at {path}")
+        lib = ctypes.CDLL(path)
+        P, I32, I64, U64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64
+        lib.kpp_status_string.argtypes = [ctypes.c_int]
+        lib.kpp_status_string.restype = ctypes.c_char_p
+        lib.kpp_version.argtypes = []
+        lib.kpp_version.restype = I32
+        lib.kpp_workspace_size.argtypes = [I64, I32, I32, ctypes.c_int, P]
+        lib.kpp_workspace_size.restype = ctypes.c_size_t
+        lib.kpp_seed.argtypes = [P, P, I64, I32, I32, ctypes.c_int, U64, U64, P, I32, P, P, P,
+                                 P, ctypes.c_size_t, P, P]
+        lib.kpp_seed.restype = ctypes.c_int
+        lib.kpp_seed_host.argtypes = [P, P, P, P, I64, I32, I32, ctypes.c_int, U64, U64, P, P, P,
+                                      P, P, P, P, ctypes.c_size_t, P, P]
+        lib.kpp_seed_host.restype = ctypes.c_int
+        lib.kpp_read_status.argtypes = [P, P]
+        lib.kpp_read_status.restype = ctypes.c_int
+        lib.kpp_quantize.argtypes = [P, I64, I32, ctypes.c_int, P, P, P]
+        lib.kpp_quantize.restype = ctypes.c_int
+        _lib = lib
+        return lib
+
+
+def _opts_ptr(opts):
+    if opts is None:
+        return None
+    if isinstance(opts, dict):
+        o = Options()
+        for k, v in opts.items():
+            setattr(o, k, v)
+        opts = o
+    return ctypes.byref(opts)
+
+
+# ---------------------------------------------------------------------------
+# C entry points, same names and argument order as include/kpp.h.
+# ---------------------------------------------------------------------------
+def kpp_status_string(status: int) -> str:
+    return load_library().kpp_status_string(int(status)).decode()
+
+
+def kpp_version() -> int:
+    return load_library().kpp_version()
+
+
+def kpp_workspace_size(N, d, K, dtype, opts=None) -> int:
+    return load_library().kpp_workspace_size(N, d, K, dtype, _opts_ptr(opts))
+
+
+def kpp_seed(points, row_scales, N, d, K, dtype, seed, stream_id, forced_prefix, n_forced,
+             indices_out, d2_out, phi_out, workspace, workspace_bytes, stream, opts=None) -> int:
+    return load_library().kpp_seed(points, row_scales, N, d, K, dtype, seed, stream_id,
+                                   forced_prefix, n_forced, indices_out, d2_out, phi_out,
+                                   workspace, workspace_bytes, stream, _opts_ptr(opts))
+
+
+def kpp_seed_host(host_points, host_scales, dev_points, dev_scales, N, d, K, dtype, seed,
+                  stream_id, host_indices, host_d2, host_phi, dev_indices, dev_d2, dev_phi,
+                  workspace, workspace_bytes, stream, opts=None) -> int:
+    return load_library().kpp_seed_host(host_points, host_scales, dev_points, dev_scales, N, d,
+                                        K, dtype, seed, stream_id, host_indices, host_d2,
+                                        host_phi, dev_indices, dev_d2, dev_phi, workspace,
+                                        workspace_bytes, stream, _opts_ptr(opts))
+
+
+def kpp_read_status(workspace, stream) -> int:
+    return load_library().kpp_read_status(workspace, stream)
+
+
+def kpp_quantize(x, N, d, to, out, row_scales, stream) -> int:
+    return load_library().kpp_quantize(x, N, d, to, out, row_scales, stream)
+
+
+# ---------------------------------------------------------------------------
+# Tensor helpers.
+# ---------------------------------------------------------------------------
+def _dtype_code(points, dtype):
+    import torch
+
+    if dtype is not None:
+        return _DTYPE_NAMES[dtype] if isinstance(dtype, str) else int(dtype)
+    if points.dtype == torch.float32:
+        return F32
+    if points.dtype in (torch.bfloat16, torch.int16, torch.uint16):
+        return BF16
+    if points.dtype in (torch.uint8, torch.float8_e4m3fn):
+        return FP8_E4M3
+    raise TypeError(f"unsupported point dtype {points.dtype}")
+
+
+def _stream_handle(device):
+    import torch
+
+    return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+def workspace_for(N, d, K, dtype, device, opts=None):
+    """A torch uint8 workspace tensor of the size kpp_workspace_size reports."""
+    import torch
+
+    with torch.cuda.device(device):
+        n = kpp_workspace_size(N, d, K, dtype, opts)
+    # 0 means the arguments are rejected; kpp_seed then reports why.
+    return torch.empty(max(n, 256), dtype=torch.uint8, device=device)
+
+
+def seed(points, K: int, seed: int, stream_id: int = 0, *, dtype=None, row_scales=None,
+         forced=None, opts=None, workspace=None, out=None, check: bool = True):
+    """k-means++ seeding on the GPU through ``kpp_seed``.
+
+    ``points``: CUDA tensor [N, d] of float32, BF16 bits (bfloat16/int16) or
+    E4M3 codes (uint8/float8_e4m3fn, with ``row_scales`` float32 [N]).
+    Returns ``(idx int64 [K], d2 float32 [N], phi float64 [1])`` on the same
+    device.  With ``check`` the stream is synchronised and a device status
+    other than OK raises ``KppError`` (degenerate data included); without it
+    the call stays asynchronous.
+    """
+    import torch
+
+    if not points.is_cuda:
+        raise ValueError("points must be a CUDA tensor (use seed_host for host data)")
+    N, d = points.shape
+    dt = _dtype_code(points, dtype)
+    dev = points.device
+    if out is None:
+        idx = torch.empty(K, dtype=torch.int64, device=dev)
+        d2 = torch.empty(N, dtype=torch.float32, device=dev)
+        phi = torch.empty(1, dtype=torch.float64, device=dev)
+    else:
+        idx, d2, phi = out
+    ws = workspace if workspace is not None else workspace_for(N, d, K, dt, dev, opts)
+    fo = None
+    if forced is not None:
+        fo = torch.as_tensor(forced, dtype=torch.int64, device=dev).contiguous()
+    with torch.cuda.device(dev):
+        st = kpp_seed(points.data_ptr(), None if row_scales is None else row_scales.data_ptr(),
+                      N, d, K, dt, seed, stream_id, None if fo is None else fo.data_ptr(),
+                      0 if fo is None else fo.numel(), idx.data_ptr(), d2.data_ptr(),
+                      phi.data_ptr(), ws.data_ptr(), ws.numel(), _stream_handle(dev), opts)
+        if st != OK:
+            raise KppError(st, "kpp_seed")
+        if check:
+            st = kpp_read_status(ws.data_ptr(), _stream_handle(dev))
+            if st != OK:
+                raise KppError(st, "kpp_seed (device)")
+    return idx, d2, phi
+
+
+def seed_host(points_host, K: int, seed: int, stream_id: int = 0, *, dtype=None,
+              row_scales_host=None, device="cuda", opts=None, buffers=None):
+    """End-to-end seeding from host (ideally pinned) tensors via ``kpp_seed_host``.
+
+    Returns host tensors ``(idx, d2, phi)`` and the device status.
+    ``buffers`` may carry reusable device/host buffers from a previous call
+    (the dict this function returns as its last element).
+    """
+    import torch
+
+    N, d = points_host.shape
+    dt = _dtype_code(points_host, dtype)
+    b = buffers
+    if b is None:
+        b = {
+            "dev_points": torch.empty_like(points_host, device=device),
+            "dev_scales": (torch.empty(N, dtype=torch.float32, device=device)
+                           if dt == FP8_E4M3 else None),
+            "dev_idx": torch.empty(K, dtype=torch.int64, device=device),
+            "dev_d2": torch.empty(N, dtype=torch.float32, device=device),
+            "dev_phi": torch.empty(1, dtype=torch.float64, device=device),
+            "host_idx": torch.empty(K, dtype=torch.int64, pin_memory=True),
+            "host_d2": torch.empty(N, dtype=torch.float32, pin_memory=True),
+            "host_phi": torch.empty(1, dtype=torch.float64, pin_memory=True),
+            "ws": workspace_for(N, d, K, dt, torch.device(device), opts),
+        }
+    dev = b["dev_idx"].device
+    with torch.cuda.device(dev):
+        st = kpp_seed_host(
+            points_host.data_ptr(),
+            None if row_scales_host is None else row_scales_host.data_ptr(),
+            b["dev_points"].data_ptr(),
+            None if b["dev_scales"] is None else b["dev_scales"].data_ptr(),
+            N, d, K, dt, seed, stream_id, b["host_idx"].data_ptr(), b["host_d2"].data_ptr(),
+            b["host_phi"].data_ptr(), b["dev_idx"].data_ptr(), b["dev_d2"].data_ptr(),
+            b["dev_phi"].data_ptr(), b["ws"].data_ptr(), b["ws"].numel(), _stream_handle(dev),
+            opts)
+    return b["host_idx"], b["host_d2"], b["host_phi"], st, b
+
+
+def quantize(x, to: str, *, out=None, row_scales=None):
+    """FP32 CUDA points [N, d] -> BF16 bits (int16 tensor) or (E4M3 uint8, scales)."""
+    import torch
+
+    N, d = x.shape
+    code = _DTYPE_NAMES[to]
+    if code == BF16:
+        q = out if out is not None else torch.empty((N, d), dtype=torch.int16, device=x.device)
+        s = None
+    elif code == FP8_E4M3:
+        q = out if out is not None else torch.empty((N, d), dtype=torch.uint8, device=x.device)
+        s = row_scales if row_scales is not None else torch.empty(N, dtype=torch.float32,
+                                                                  device=x.device)
+    else:
+        raise ValueError(to)
+    with torch.cuda.device(x.device):
+        st = kpp_quantize(x.data_ptr(), N, d, code, q.data_ptr(),
+                          None if s is None else s.data_ptr(), _stream_handle(x.device))
+    if st != OK:
+        raise KppError(st, "kpp_quantize")
+    return q if s is None else (q, s)

@@ -1,0 +1,69 @@
+"""The C ABI library builds, loads, and exports every entry point that
+include/kpp.h declares (no GPU needed: only host-side functions are called)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_entry_points():
+    names = []
+    for fn in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if fn.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", fn)).read()
+            names += re.findall(r"KPP_API\s+[\w\s\*]+?\b(kpp_\w+)\s*\(", txt)
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import paper_1908_02136_gb300 as kpp
+
+    return kpp.load_library()
+
+
+def test_header_declares_the_boundary():
+    names = declared_entry_points()
+    for required in ["kpp_seed", "kpp_workspace_size", "kpp_read_status", "kpp_quantize",
+                     "kpp_seed_host", "kpp_status_string", "kpp_version"]:
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    import paper_1908_02136_gb300 as kpp
+
+    out = subprocess.run(["nm", "-D", "--defined-only", kpp.library_path()],
+                         capture_output=True, text=True, check=True).stdout
+    exported = set(re.findall(r"\bT\s+(\w+)", out))
+    for name in declared_entry_points():
+        assert name in exported, name
+        assert hasattr(lib, name)
+    # nothing but the declared C names leaks out of the library
+    ours = {n for n in exported if n.startswith("kpp")}
+    assert ours == set(declared_entry_points())
+
+
+def test_host_only_entry_points(lib):
+    import paper_1908_02136_gb300 as kpp
+
+    assert kpp.kpp_version() >= 100
+    for code in range(8):
+        s = kpp.kpp_status_string(code)
+        assert isinstance(s, str) and s and s != "unknown status"
+    assert kpp.kpp_status_string(99) == "unknown status"
+
+
+def test_invalid_arguments_fail_synchronously(lib):
+    import paper_1908_02136_gb300 as kpp
+
+    # NULL points / K > N / bad dtype are rejected before any CUDA call
+    assert kpp.kpp_seed(None, None, 10, 2, 3, 0, 1, 0, None, 0, None, None, None,
+                        None, 0, None) == kpp.ERR_INVALID_ARG
+    assert kpp.kpp_workspace_size(10, 2, 11, 0) == 0
+    assert kpp.kpp_workspace_size(10, 0, 1, 0) == 0
+    assert kpp.kpp_workspace_size(10, 2, 1, 7) == 0
+    assert kpp.kpp_quantize(None, 4, 4, kpp.BF16, None, None, None) == kpp.ERR_INVALID_ARG

@@ -1,0 +1,206 @@
+"""GPU parity of the streamed seeding path (through the C ABI) against the FP64
+oracle: bit-exact in the integer regime, within 1e-5 relative D^2 and the
+near-boundary draw band in the float regime, for every stored dtype, ragged
+sizes, the generic kernel, every lanes-per-row specialisation, graph and
+plain launches, degenerate data and forced prefixes."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import parity
+import paper_1908_02136_gb300 as kpp
+from paper_1908_02136_gb300 import datagen
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda:0"
+
+
+def run(points_np, K, seed, stream_id=0, *, dtype="f32", opts=None, forced=None, check=True):
+    """Stores the points as `dtype` on the GPU (quantising with the library)
+    and seeds; returns numpy (stored points, scales, idx, d2, phi)."""
+    x = torch.from_numpy(points_np).to(DEV)
+    scales = None
+    if dtype == "f32":
+        stored = x
+        stored_np = points_np
+    elif dtype == "bf16":
+        stored = kpp.quantize(x, "bf16")
+        stored_np = stored.cpu().numpy().view(np.uint16)
+    else:
+        stored, scales = kpp.quantize(x, "fp8")
+        stored_np = stored.cpu().numpy()
+    idx, d2, phi = kpp.seed(stored, K, seed, stream_id, dtype=dtype, row_scales=scales,
+                            opts=opts, forced=forced, check=check)
+    torch.cuda.synchronize()
+    sc = None if scales is None else scales.cpu().numpy()
+    return stored_np, sc, idx.cpu().numpy(), d2.cpu().numpy(), float(phi.cpu()[0])
+
+
+EXACT_SHAPES = [(5000, 2, 16), (7777, 4, 33), (4097, 8, 40), (20011, 16, 64), (20011, 32, 64),
+                (3001, 64, 20), (4099, 128, 12), (1000, 3, 10), (999, 5, 9), (2500, 96, 8)]
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+@pytest.mark.parametrize("N,d,K", EXACT_SHAPES)
+def test_exact_regime_bit_identical(N, d, K, dtype):
+    x = datagen.integer_points(N, d, seed=N + d, n_comp=8)
+    st, sc, idx, d2, phi = run(x, K, seed=17, dtype=dtype)
+    parity.check(st, K, 17, 0, idx, d2, phi, scales=sc, exact=True)
+
+
+@pytest.mark.parametrize("N,d,K,ncomp", [(10_000, 2, 16, 16), (100_003, 32, 64, 64),
+                                         (50_001, 64, 48, 32), (30_011, 128, 32, 32),
+                                         (12_345, 8, 100, 50), (9_999, 7, 20, 10)])
+def test_float_regime_f32(N, d, K, ncomp):
+    x = datagen.gmm(N, d, ncomp, seed=N, mean_box=50.0)
+    st, sc, idx, d2, phi = run(x, K, seed=1)
+    events = parity.check(st, K, 1, 0, idx, d2, phi)
+    assert events <= 1
+
+
+def test_paper_scale_small_workload():
+    wl = datagen.WORKLOADS["gmm-N1e4-d2-K16"]
+    x = datagen.workload_points(wl)
+    st, sc, idx, d2, phi = run(x, wl.K, seed=wl.draw_seed)
+    assert parity.check(st, wl.K, wl.draw_seed, 0, idx, d2, phi) == 0
+
+
+@pytest.mark.parametrize("dtype", ["bf16", "fp8"])
+@pytest.mark.parametrize("N,d,K", [(40_003, 16, 32), (20_001, 64, 24), (10_007, 128, 16),
+                                   (8_191, 2, 12), (6_001, 4, 12), (5_003, 8, 10)])
+def test_float_regime_low_precision_storage(N, d, K, dtype):
+    x = datagen.gmm(N, d, K, seed=N + 1, mean_box=50.0)
+    st, sc, idx, d2, phi = run(x, K, seed=5, dtype=dtype)
+    events = parity.check(st, K, 5, 0, idx, d2, phi, scales=sc)
+    assert events <= 1
+
+
+@pytest.mark.parametrize("d,lanes", [(8, 1), (8, 2), (16, 2), (16, 4), (32, 2), (32, 4),
+                                     (32, 8), (64, 4), (64, 8), (64, 16), (128, 8), (128, 16),
+                                     (128, 32)])
+def test_every_lanes_per_row_variant(d, lanes):
+    x = datagen.integer_points(9001, d, seed=d * lanes, n_comp=6)
+    opts = {"lanes_per_row": lanes}
+    st, sc, idx, d2, phi = run(x, 24, seed=3, opts=opts)
+    parity.check(st, 24, 3, 0, idx, d2, phi, exact=True)
+
+
+def test_unbuilt_lanes_variant_is_rejected():
+    x = torch.zeros((100, 32), device=DEV)
+    with pytest.raises(kpp.KppError) as e:
+        kpp.seed(x, 4, 1, opts={"lanes_per_row": 32})
+    assert e.value.status == kpp.ERR_UNSUPPORTED
+
+
+def test_graph_and_plain_launches_agree_and_repeat():
+    x = datagen.gmm(60_000, 32, 32, seed=2)
+    a = run(x, 40, seed=9)
+    b = run(x, 40, seed=9, opts={"use_graph": -1})
+    c = run(x, 40, seed=9)  # graph cache hit
+    for other in (b, c):
+        assert np.array_equal(a[2], other[2])
+        assert np.array_equal(a[3], other[3])
+        assert a[4] == other[4]
+
+
+def test_ctas_per_sm_changes_blocking_not_results_in_exact_regime():
+    x = datagen.integer_points(50_000, 16, seed=4, n_comp=8)
+    ref = run(x, 30, seed=4)
+    for per_sm in (1, 2, 3):
+        o = run(x, 30, seed=4, opts={"ctas_per_sm": per_sm})
+        assert np.array_equal(ref[2], o[2]) and np.array_equal(ref[3], o[3])
+
+
+def test_k1_and_k_equals_n():
+    x = datagen.gmm(257, 4, 4, seed=8)
+    st, sc, idx, d2, phi = run(x, 1, seed=2)
+    parity.check(st, 1, 2, 0, idx, d2, phi)
+    st, sc, idx, d2, phi = run(x, 257, seed=2)
+    assert sorted(idx.tolist()) == list(range(257))
+    assert np.all(d2 == 0) and phi == 0.0
+
+
+def test_single_point():
+    x = np.array([[1.5, -2.0]], np.float32)
+    st, sc, idx, d2, phi = run(x, 1, seed=0)
+    assert idx.tolist() == [0] and d2.tolist() == [0.0] and phi == 0.0
+
+
+def test_degenerate_data_reports_status():
+    base = np.array([[0, 0, 0, 0], [1, 2, 3, 4], [5, 5, 5, 5]], np.float32)
+    x = np.repeat(base, [400, 300, 301], axis=0)
+    rng = np.random.default_rng(0)
+    x = x[rng.permutation(len(x))]
+    with pytest.raises(kpp.KppError) as e:
+        run(x, 5, seed=1)
+    assert e.value.status == kpp.ERR_DEGENERATE
+    st, sc, idx, d2, phi = run(x, 5, seed=1, check=False)
+    assert np.all(idx[3:] == -1) and phi == 0.0
+    parity.check(st, 5, 1, 0, idx, d2, phi, exact=True, status=oracle.DEGENERATE)
+
+
+def test_forced_prefix_replays_the_oracle():
+    x = datagen.gmm(30_000, 16, 16, seed=6)
+    r = oracle.seed(x, 20, 4)
+    st, sc, idx, d2, phi = run(x, 20, seed=4, forced=r["idx"])
+    assert np.array_equal(idx, r["idx"])
+    np.testing.assert_allclose(d2, r["d2"], rtol=1e-5)
+    # a partial prefix: the GPU continues with its own draws after it
+    st, sc, idx2, d2, phi = run(x, 20, seed=4, forced=r["idx"][:7])
+    assert np.array_equal(idx2[:7], r["idx"][:7])
+    parity.check(st, 20, 4, 0, idx2, d2, phi)
+
+
+def test_bad_forced_index_is_a_device_error():
+    x = torch.zeros((64, 4), device=DEV)
+    x[:, 0] = torch.arange(64, device=DEV, dtype=torch.float32)
+    with pytest.raises(kpp.KppError) as e:
+        kpp.seed(x, 3, 1, forced=[5, 64])
+    assert e.value.status == kpp.ERR_INVALID_ARG
+
+
+def test_streams_give_independent_draws():
+    x = datagen.gmm(20_000, 8, 16, seed=9)
+    a = run(x, 16, seed=1, stream_id=0)
+    b = run(x, 16, seed=1, stream_id=1)
+    assert not np.array_equal(a[2], b[2])
+    parity.check(b[0], 16, 1, 1, b[2], b[3], b[4])
+
+
+def test_quantizers_match_the_oracle_bit_for_bit():
+    x = datagen.gmm(33_333, 24, 8, seed=3, mean_box=80.0)
+    x[5] = 0.0
+    xt = torch.from_numpy(x).to(DEV)
+    qb = kpp.quantize(xt, "bf16").cpu().numpy().view(np.uint16)
+    assert np.array_equal(qb, oracle.quantize_bf16(x))
+    q8, s8 = kpp.quantize(xt, "fp8")
+    oq, os_ = oracle.quantize_fp8(x)
+    assert np.array_equal(s8.cpu().numpy(), os_)
+    assert np.array_equal(q8.cpu().numpy(), oq)
+    # odd element count for the BF16 tail
+    y = x.ravel()[:1001].reshape(1001, 1).copy()
+    qy = kpp.quantize(torch.from_numpy(y).to(DEV), "bf16").cpu().numpy().view(np.uint16)
+    assert np.array_equal(qy, oracle.quantize_bf16(y))
+
+
+def test_seed_host_matches_device_seed():
+    x = datagen.gmm(70_001, 32, 32, seed=11)
+    st, sc, idx, d2, phi = run(x, 32, seed=2)
+    xh = torch.from_numpy(x).pin_memory()
+    hidx, hd2, hphi, status, _ = kpp.seed_host(xh, 32, 2)
+    assert status == kpp.OK
+    assert np.array_equal(hidx.numpy(), idx)
+    assert np.array_equal(hd2.numpy(), d2)
+    assert float(hphi[0]) == phi
+
+
+@pytest.mark.slow
+def test_full_size_workload_parity():
+    """The bench workload (10^6 x 32, K=256) in the bench's launch configuration."""
+    wl = datagen.WORKLOADS["gmm-N1e6-d32-K256"]
+    x = datagen.workload_points(wl)
+    st, sc, idx, d2, phi = run(x, wl.K, seed=wl.draw_seed)
+    events = parity.check(st, wl.K, wl.draw_seed, 0, idx, d2, phi)
+    assert events <= 2
