@@ -47,6 +47,10 @@ def parse():
     ap.add_argument("--form", type=int, default=0)
     ap.add_argument("--lanes", type=int, default=0)
     ap.add_argument("--ctas-per-sm", type=int, default=0)
+    ap.add_argument("--smem-cache", type=int, default=0)
+    ap.add_argument("--alternate", type=int, default=0)
+    ap.add_argument("--l2-policy", type=int, default=0)
+    ap.add_argument("--min-rows", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
@@ -217,7 +221,17 @@ def main():
     opts.form = args.form
     opts.lanes_per_row = args.lanes
     opts.ctas_per_sm = args.ctas_per_sm
+    opts.smem_cache = args.smem_cache
+    opts.alternate = args.alternate
+    opts.l2_policy = args.l2_policy
+    opts.min_rows_per_cta = args.min_rows
     code = {"f32": kpp.F32, "bf16": kpp.BF16, "fp8": kpp.FP8_E4M3}[args.dtype]
+    with torch.cuda.device(dev):
+        pst, plan = kpp.kpp_describe(N, d, K, code, opts)
+    if pst != kpp.OK:
+        raise kpp.KppError(pst, "kpp_describe")
+    plan = plan.as_dict()
+    form_name = {kpp.FORM_STREAMED: "streamed", kpp.FORM_PERSISTENT: "persistent"}[plan["form"]]
     ws = kpp.workspace_for(N, d, K, code, dev, opts)
     idx = torch.empty(K, dtype=torch.int64, device=dev)
     d2 = torch.empty(N, dtype=torch.float32, device=dev)
@@ -301,18 +315,22 @@ def main():
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "ms_per_step": 1e3 * e2e_s / e2e_steps}
 
-    # roofline of the dominant kernel (the per-pass streamed kernel)
+    # roofline of the dominant kernel: the persistent kernel (one launch per
+    # seeding) or the per-pass streamed kernel (K launches per seeding)
     peaks = measured_peaks()
     peak = peaks["hbm_gbs"] if peaks else 6800.0
-    launches_per_step = K
+    launches_per_step = plan["launches"]
     per_launch_ms = ms_per_step / launches_per_step
-    alg_bytes = N * d * eb + (4 * N if scales is not None else 0) + 8 * N
+    passes_per_launch = K // launches_per_step
+    point_bytes = N * d * eb + (4 * N if scales is not None else 0)
+    d2_bytes = 8 * N if form_name == "streamed" else 0  # D^2 stays on chip when persistent
+    alg_bytes = passes_per_launch * (point_bytes + d2_bytes)
     achieved = alg_bytes / (per_launch_ms / 1e3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": None,
                 "peak_source": "measured" if peaks else "fallback",
-                "algorithmic_bytes_per_launch": alg_bytes,
-                "points_only_frac": (N * d * eb) / (per_launch_ms / 1e3) / 1e9 / peak}
+                "kernel": f"{form_name}_kernel", "algorithmic_bytes_per_launch": alg_bytes,
+                "algorithmic_bytes_per_pass": point_bytes + d2_bytes}
 
     cpu_baseline = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -338,7 +356,7 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": args.dtype, "data": "synthetic",
             "config": {"workload": wl.name, "N": N, "d": d, "K": K, "storage": args.dtype,
-                       "form": "streamed", "parallelism": f"replicas{world}",
+                       "form": form_name, "plan": plan, "parallelism": f"replicas{world}",
                        "l2": "flushed between steps (512 MiB write)",
                        "step_ms_min": min(step_ms), "step_ms_max": max(step_ms)},
             "clocks": clocks, "e2e": e2e, "gpu_launches": launches_per_step * args.steps,

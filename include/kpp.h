@@ -87,13 +87,38 @@ typedef enum {
 
 /* Tuning knobs; a zeroed struct (or NULL) means "choose automatically". */
 typedef struct {
-    int32_t form;          /* kpp_form */
-    int32_t lanes_per_row; /* lanes that share one point row: 1,2,4,8,16,32 */
-    int32_t ctas_per_sm;   /* resident CTAs per SM the grid is sized for */
-    int32_t use_graph;     /* streamed form: 0/1 = CUDA graph, -1 = plain launches */
-    uint32_t timeout_us;   /* bounded device waits; 0 = 2,000,000 us */
+    int32_t form;             /* kpp_form */
+    int32_t lanes_per_row;    /* lanes that share one point row: 1,2,4,8,16,32 */
+    int32_t ctas_per_sm;      /* resident CTAs per SM the grid is sized for */
+    int32_t use_graph;        /* streamed form: 0/1 = CUDA graph, -1 = plain launches */
+    uint32_t timeout_us;      /* persistent form: bound of each grid-barrier wait;
+                                 0 = 2,000,000 us */
+    int32_t smem_cache;       /* persistent form: -1 = no shared-memory point cache,
+                                 0 = as many rows as fit, > 0 = at most this many
+                                 rows per CTA */
+    int32_t alternate;        /* persistent form: 0/1 = walk rows backwards on odd
+                                 passes (L2 reuse), -1 = always forwards */
+    int32_t l2_policy;        /* persistent form, streamed rows: 0 = evict-last,
+                                 -1 = no hint, 2 = evict-first */
+    int32_t min_rows_per_cta; /* persistent form: smallest row block; 0 = 2048 */
     int32_t reserved[3];
 } kpp_options;
+
+/* The launch plan kpp_seed would use for a problem (filled by kpp_describe). */
+typedef struct {
+    int32_t form;                /* kpp_form actually chosen */
+    int32_t grid;                /* CTAs per launch */
+    int32_t threads;             /* threads per CTA */
+    int32_t launches;            /* kernel launches per seeding */
+    int32_t lanes_per_row;       /* 0 for the generic (any d) kernel */
+    int32_t d2_in_smem;          /* persistent form: D^2 held in shared memory */
+    int64_t rows_per_cta;        /* contiguous row block of each CTA */
+    int64_t rows_per_segment;    /* rows under one middle-level sum of the draw
+                                    (one warp's contiguous share of a block) */
+    int64_t cached_rows_per_cta; /* persistent form: rows kept in shared memory */
+    int64_t smem_bytes;          /* dynamic shared memory per CTA */
+    int64_t workspace_bytes;     /* same as kpp_workspace_size */
+} kpp_plan;
 
 /* Human-readable name of a status code (static string, never NULL). */
 KPP_API const char *kpp_status_string(kpp_status status);
@@ -108,6 +133,14 @@ KPP_API int32_t kpp_version(void);
  */
 KPP_API size_t kpp_workspace_size(int64_t N, int32_t d, int32_t K, kpp_dtype dtype,
                           const kpp_options *opts);
+
+/*
+ * Fills `plan` with the form, grid and memory layout kpp_seed would use for
+ * these arguments on the current device.  Host-side only; nothing is
+ * launched.  Returns KPP_OK or the error kpp_seed would return.
+ */
+KPP_API kpp_status kpp_describe(int64_t N, int32_t d, int32_t K, kpp_dtype dtype,
+                                const kpp_options *opts, kpp_plan *plan);
 
 /*
  * k-means++ seeding of one problem (Algorithm 1 / Algorithm 2).

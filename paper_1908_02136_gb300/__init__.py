@@ -7,6 +7,7 @@ only marshals arguments.  PyTorch supplies device memory and streams.
 Two layers:
 
 * the C entry points under their C names (``kpp_seed``, ``kpp_workspace_size``,
+  ``kpp_describe``,
   ``kpp_read_status``, ``kpp_quantize``, ``kpp_seed_host``,
   ``kpp_status_string``, ``kpp_version``), taking raw pointers and sizes;
 * tensor helpers (``seed``, ``seed_host``, ``quantize``) that allocate the
@@ -44,7 +45,22 @@ class Options(ctypes.Structure):
 
     _fields_ = [("form", ctypes.c_int32), ("lanes_per_row", ctypes.c_int32),
                 ("ctas_per_sm", ctypes.c_int32), ("use_graph", ctypes.c_int32),
-                ("timeout_us", ctypes.c_uint32), ("reserved", ctypes.c_int32 * 3)]
+                ("timeout_us", ctypes.c_uint32), ("smem_cache", ctypes.c_int32),
+                ("alternate", ctypes.c_int32), ("l2_policy", ctypes.c_int32),
+                ("min_rows_per_cta", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+
+
+class Plan(ctypes.Structure):
+    """Mirror of kpp_plan."""
+
+    _fields_ = [("form", ctypes.c_int32), ("grid", ctypes.c_int32), ("threads", ctypes.c_int32),
+                ("launches", ctypes.c_int32), ("lanes_per_row", ctypes.c_int32),
+                ("d2_in_smem", ctypes.c_int32), ("rows_per_cta", ctypes.c_int64),
+                ("rows_per_segment", ctypes.c_int64), ("cached_rows_per_cta", ctypes.c_int64),
+                ("smem_bytes", ctypes.c_int64), ("workspace_bytes", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
 
 
 _lock = threading.Lock()
@@ -72,6 +88,8 @@ def load_library(build_if_stale: bool = True):
         lib.kpp_version.restype = I32
         lib.kpp_workspace_size.argtypes = [I64, I32, I32, ctypes.c_int, P]
         lib.kpp_workspace_size.restype = ctypes.c_size_t
+        lib.kpp_describe.argtypes = [I64, I32, I32, ctypes.c_int, P, P]
+        lib.kpp_describe.restype = ctypes.c_int
         lib.kpp_seed.argtypes = [P, P, I64, I32, I32, ctypes.c_int, U64, U64, P, I32, P, P, P,
                                  P, ctypes.c_size_t, P, P]
         lib.kpp_seed.restype = ctypes.c_int
@@ -91,7 +109,10 @@ def _opts_ptr(opts):
         return None
     if isinstance(opts, dict):
         o = Options()
+        names = {f for f, _ in Options._fields_}
         for k, v in opts.items():
+            if k not in names:
+                raise KeyError(f"unknown kpp_options field {k!r}")
             setattr(o, k, v)
         opts = o
     return ctypes.byref(opts)
@@ -110,6 +131,13 @@ def kpp_version() -> int:
 
 def kpp_workspace_size(N, d, K, dtype, opts=None) -> int:
     return load_library().kpp_workspace_size(N, d, K, dtype, _opts_ptr(opts))
+
+
+def kpp_describe(N, d, K, dtype, opts=None, plan=None):
+    """Returns (status, Plan) for the launch plan kpp_seed would use."""
+    plan = plan if plan is not None else Plan()
+    st = load_library().kpp_describe(N, d, K, dtype, _opts_ptr(opts), ctypes.byref(plan))
+    return st, plan
 
 
 def kpp_seed(points, row_scales, N, d, K, dtype, seed, stream_id, forced_prefix, n_forced,

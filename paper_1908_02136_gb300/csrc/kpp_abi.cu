@@ -32,10 +32,18 @@ int elem_bytes(int dt) { return dt == KPP_F32 ? 4 : dt == KPP_BF16 ? 2 : 1; }
 
 struct Plan {
     int form;
-    StreamedKernel sk;
-    int grid;       // CTAs per launch
-    int64_t chunk;  // rows per CTA
-    int nblocks;    // CTAs owning rows (== grid for the streamed form)
+    StreamedKernel sk;   // streamed form
+    PersistentKernel pk; // persistent form
+    const void *pfn;     // persistent kernel chosen (D^2 in smem or ping-pong)
+    size_t psmem;        // its dynamic shared memory
+    PersistArgs pargs;
+    int grid;      // CTAs per launch (== nblocks)
+    int64_t chunk; // rows per CTA
+    int nblocks;
+    int nseg;   // segments (warps) per block
+    int64_t sw; // rows per super-iteration
+    // workspace layout (byte offsets after the control block)
+    size_t off_bsum, off_seg, off_slots;
     size_t ws_bytes;
 };
 
@@ -43,6 +51,143 @@ bool shape_ok(int64_t N, int32_t d, int32_t K, int dt)
 {
     return N >= 1 && N < (int64_t(1) << 31) && d >= 1 && d <= kMaxDim && K >= 1 && K <= N &&
            dt >= KPP_F32 && dt <= KPP_FP8_E4M3;
+}
+
+void layout(Plan *pl, bool persistent)
+{
+    size_t off = sizeof(Control);
+    pl->off_bsum = pl->off_seg = pl->off_slots = off;
+    if (persistent) {
+        // two buffers of tagged block sums, one 32-byte slot per block
+        off += round_up(2 * sizeof(unsigned long long) * kSlotWords * (size_t)pl->nblocks, kAlign);
+    } else {
+        off += round_up(sizeof(float2) * (size_t)pl->nblocks, kAlign);
+        pl->off_seg = off;
+        off += round_up(sizeof(float2) * (size_t)pl->nblocks * pl->nseg, kAlign);
+    }
+    pl->ws_bytes = off;
+}
+
+kpp_status plan_streamed(int64_t N, int32_t d, int dt, const kpp_options &o, int sms, Plan *pl)
+{
+    if (!streamed_lookup(dt, d, o.lanes_per_row, &pl->sk))
+        return KPP_ERR_UNSUPPORTED;
+    int per_sm = o.ctas_per_sm > 0 ? o.ctas_per_sm : kDefaultCtasPerSm;
+    if (per_sm > 32)
+        return KPP_ERR_INVALID_ARG;
+    int resident = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, pl->sk.fn, streamed_threads(),
+                                                      streamed_smem(pl->sk, d)) != cudaSuccess)
+        return KPP_ERR_CUDA;
+    if (resident >= 1 && per_sm > resident)
+        per_sm = resident; // one wave: every CTA resident at once
+    int64_t target = (int64_t)sms * per_sm;
+    if (target > kStage)
+        target = kStage; // the draw stages every block sum at once
+    const int64_t a = pl->sk.rows_align;
+    int64_t chunk = (N + target - 1) / target;
+    chunk = (chunk + a - 1) / a * a;
+    pl->form = KPP_FORM_STREAMED;
+    pl->chunk = chunk;
+    pl->nblocks = (int)((N + chunk - 1) / chunk);
+    pl->grid = pl->nblocks;
+    pl->nseg = streamed_segments();
+    pl->sw = a;
+    layout(pl, false);
+    return KPP_OK;
+}
+
+kpp_status plan_persistent_at(int64_t N, int32_t K, const kpp_options &o, int sms, int per_sm,
+                              Plan *pl);
+
+// The persistent plan at the requested CTAs per SM, or fewer if that many
+// cannot be co-resident.
+kpp_status plan_persistent(int64_t N, int32_t d, int32_t K, int dt, const kpp_options &o, int sms,
+                           Plan *pl)
+{
+    if (!persistent_lookup(dt, d, o.lanes_per_row, &pl->pk))
+        return KPP_ERR_UNSUPPORTED;
+    int per_sm = o.ctas_per_sm > 0 ? o.ctas_per_sm : 1;
+    if (per_sm > 4)
+        return KPP_ERR_INVALID_ARG;
+    kpp_status st = KPP_ERR_UNSUPPORTED;
+    for (; per_sm >= 1; --per_sm) {
+        st = plan_persistent_at(N, K, o, sms, per_sm, pl);
+        if (st != KPP_ERR_UNSUPPORTED)
+            return st;
+    }
+    return st;
+}
+
+kpp_status plan_persistent_at(int64_t N, int32_t K, const kpp_options &o, int sms, int per_sm,
+                              Plan *pl)
+{
+    int dev = 0, coop = 0, optin = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) !=
+            cudaSuccess)
+        return KPP_ERR_CUDA;
+    if (!coop)
+        return KPP_ERR_UNSUPPORTED;
+    const int64_t a = pl->pk.rows_align;
+    const int64_t min_rows = o.min_rows_per_cta > 0 ? o.min_rows_per_cta : 2048;
+    const int64_t target = (int64_t)sms * per_sm;
+    int64_t chunk = (N + target - 1) / target;
+    if (chunk < min_rows)
+        chunk = min_rows;
+    chunk = (chunk + a - 1) / a * a;
+    const int nblocks = (int)((N + chunk - 1) / chunk);
+    if ((uint64_t)K * (uint64_t)nblocks >= (1ull << 32))
+        return KPP_ERR_UNSUPPORTED; // barrier counter range
+    // shared memory: D^2 of the block if it fits, then as many cached rows as fit
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, pl->pk.fn_smem) != cudaSuccess)
+        return KPP_ERR_CUDA;
+    const int64_t budget = ((int64_t)optin - (int64_t)fa.sharedSizeBytes - 1024) / per_sm;
+    int64_t used = 0;
+    bool d2_in_smem = (int64_t)sizeof(float) * chunk <= budget;
+    if (d2_in_smem)
+        used += (int64_t)sizeof(float) * chunk;
+    // the cache holds the first `supers` super-iterations of every warp's
+    // segment (so that all warps read the same share from shared memory)
+    const int nseg = persistent_segments();
+    const int64_t seg_supers = ((chunk / a) + nseg - 1) / nseg; // longest segment
+    const int64_t unit = (int64_t)nseg * a * pl->pk.row_bytes;  // one super per warp
+    int64_t supers = 0;
+    if (o.smem_cache >= 0) {
+        supers = (budget - used) / unit;
+        if (supers > seg_supers)
+            supers = seg_supers;
+        if (o.smem_cache > 0 && supers * nseg * a > o.smem_cache)
+            supers = (int64_t)o.smem_cache / (nseg * a);
+        if (supers < 0)
+            supers = 0;
+    }
+    pl->pfn = d2_in_smem ? pl->pk.fn_smem : pl->pk.fn_global;
+    pl->psmem = (size_t)(supers * unit + (d2_in_smem ? 4 * chunk : 0));
+    // static + dynamic shared memory above 48 KB needs the opt-in attribute
+    if (cudaFuncSetAttribute(pl->pfn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)pl->psmem) != cudaSuccess)
+        return KPP_ERR_CUDA;
+    int resident = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, pl->pfn, persistent_threads(),
+                                                      pl->psmem) != cudaSuccess)
+        return KPP_ERR_CUDA;
+    if (resident < 1 || (int64_t)nblocks > (int64_t)resident * sms)
+        return KPP_ERR_UNSUPPORTED; // cannot be co-resident
+    pl->form = KPP_FORM_PERSISTENT;
+    pl->chunk = chunk;
+    pl->nblocks = nblocks;
+    pl->grid = nblocks;
+    pl->nseg = nseg;
+    pl->sw = a;
+    pl->pargs.cache_supers = supers;
+    pl->pargs.reverse = o.alternate >= 0 ? 1 : 0;
+    pl->pargs.l2_hint = o.l2_policy == 0 ? 1 : (o.l2_policy == 2 ? 2 : 0);
+    pl->pargs.timeout_ns = 1000ull * (o.timeout_us ? o.timeout_us : 2000000u);
+    layout(pl, true);
+    return KPP_OK;
 }
 
 kpp_status make_plan(int64_t N, int32_t d, int32_t K, int dt, const kpp_options *opts, Plan *pl)
@@ -53,33 +198,23 @@ kpp_status make_plan(int64_t N, int32_t d, int32_t K, int dt, const kpp_options 
     std::memset(&o, 0, sizeof(o));
     if (opts)
         o = *opts;
-    if (o.form != KPP_FORM_AUTO && o.form != KPP_FORM_STREAMED)
-        return KPP_ERR_UNSUPPORTED;
     const int sms = device_sms();
     if (sms <= 0)
         return KPP_ERR_CUDA;
-    if (!streamed_lookup(dt, d, o.lanes_per_row, &pl->sk))
+    switch (o.form) {
+    case KPP_FORM_STREAMED:
+        return plan_streamed(N, d, dt, o, sms, pl);
+    case KPP_FORM_PERSISTENT:
+        return plan_persistent(N, d, K, dt, o, sms, pl);
+    case KPP_FORM_AUTO: {
+        kpp_status st = plan_persistent(N, d, K, dt, o, sms, pl);
+        if (st == KPP_OK || st == KPP_ERR_INVALID_ARG || st == KPP_ERR_CUDA)
+            return st;
+        return plan_streamed(N, d, dt, o, sms, pl);
+    }
+    default:
         return KPP_ERR_UNSUPPORTED;
-    int per_sm = o.ctas_per_sm > 0 ? o.ctas_per_sm : kDefaultCtasPerSm;
-    if (per_sm > 32)
-        return KPP_ERR_INVALID_ARG;
-    int resident = 0;
-    const size_t smem = pl->sk.generic ? sizeof(float) * (size_t)d : 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, pl->sk.fn, streamed_threads(),
-                                                      smem) != cudaSuccess)
-        return KPP_ERR_CUDA;
-    if (resident >= 1 && per_sm > resident)
-        per_sm = resident; // one wave: every CTA resident at once
-    const int64_t target = (int64_t)sms * per_sm;
-    int64_t chunk = (N + target - 1) / target;
-    const int64_t a = pl->sk.rows_align;
-    chunk = (chunk + a - 1) / a * a;
-    pl->form = KPP_FORM_STREAMED;
-    pl->chunk = chunk;
-    pl->nblocks = (int)((N + chunk - 1) / chunk);
-    pl->grid = pl->nblocks;
-    pl->ws_bytes = sizeof(Control) + round_up(sizeof(double) * (size_t)pl->nblocks, kAlign);
-    return KPP_OK;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -122,6 +257,17 @@ cudaError_t enqueue_streamed(const Plan &pl, const Problem &p, cudaStream_t s)
     for (int m = 0; e == cudaSuccess && m < p.K; ++m)
         e = streamed_launch(pl.sk, pl.grid, p, m, s);
     return e;
+}
+
+kpp_status run_persistent(const Plan &pl, const Problem &p, cudaStream_t stream)
+{
+    // the control block and both slot buffers start at zero: a zeroed slot
+    // never carries the tag a pass waits for
+    if (cudaMemsetAsync(p.ctl, 0, pl.ws_bytes, stream) != cudaSuccess)
+        return KPP_ERR_CUDA;
+    return persistent_launch(pl.pfn, pl.grid, pl.psmem, p, pl.pargs, stream) == cudaSuccess
+               ? KPP_OK
+               : KPP_ERR_LAUNCH;
 }
 
 kpp_status run_streamed(const Plan &pl, const Problem &p, cudaStream_t stream, int use_graph)
@@ -219,6 +365,38 @@ size_t kpp_workspace_size(int64_t N, int32_t d, int32_t K, kpp_dtype dtype,
     return pl.ws_bytes;
 }
 
+kpp_status kpp_describe(int64_t N, int32_t d, int32_t K, kpp_dtype dtype,
+                        const kpp_options *opts, kpp_plan *plan)
+{
+    if (!plan)
+        return KPP_ERR_INVALID_ARG;
+    Plan pl;
+    std::memset(&pl, 0, sizeof(pl));
+    kpp_status st = make_plan(N, d, K, (int)dtype, opts, &pl);
+    if (st != KPP_OK)
+        return st;
+    std::memset(plan, 0, sizeof(*plan));
+    plan->form = pl.form;
+    plan->grid = pl.grid;
+    plan->rows_per_cta = pl.chunk;
+    plan->rows_per_segment = (pl.chunk + pl.nseg - 1) / pl.nseg;
+    plan->workspace_bytes = (int64_t)pl.ws_bytes;
+    if (pl.form == KPP_FORM_PERSISTENT) {
+        plan->threads = persistent_threads();
+        plan->launches = 1;
+        plan->lanes_per_row = pl.pk.lanes;
+        plan->d2_in_smem = pl.pfn == pl.pk.fn_smem ? 1 : 0;
+        plan->cached_rows_per_cta = pl.pargs.cache_supers * pl.nseg * pl.sw;
+        plan->smem_bytes = (int64_t)pl.psmem;
+    } else {
+        plan->threads = streamed_threads();
+        plan->launches = K;
+        plan->lanes_per_row = pl.sk.lanes;
+        plan->smem_bytes = (int64_t)streamed_smem(pl.sk, d);
+    }
+    return KPP_OK;
+}
+
 kpp_status kpp_seed(const void *points, const float *row_scales, int64_t N, int32_t d,
                     int32_t K, kpp_dtype dtype, uint64_t seed, uint64_t stream_id,
                     const int64_t *forced_prefix, int32_t n_forced, int64_t *indices_out,
@@ -254,10 +432,21 @@ kpp_status kpp_seed(const void *points, const float *row_scales, int64_t N, int3
     p.idx = indices_out;
     p.d2 = d2_out;
     p.phi = phi_out;
-    p.ctl = reinterpret_cast<Control *>(workspace);
-    p.block_sums = reinterpret_cast<double *>(reinterpret_cast<char *>(workspace) + sizeof(Control));
+    p.nseg = pl.nseg;
+    p.sw = pl.sw;
+    char *ws = reinterpret_cast<char *>(workspace);
+    p.ctl = reinterpret_cast<Control *>(ws);
+    if (pl.form == KPP_FORM_PERSISTENT) {
+        p.slots = reinterpret_cast<unsigned long long *>(ws + pl.off_slots);
+    } else {
+        p.block_sums = reinterpret_cast<float2 *>(ws + pl.off_bsum);
+        p.seg_sums = reinterpret_cast<float2 *>(ws + pl.off_seg);
+    }
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (pl.form == KPP_FORM_PERSISTENT)
+        return run_persistent(pl, p, s);
     const int use_graph = opts ? opts->use_graph : 0;
-    return run_streamed(pl, p, reinterpret_cast<cudaStream_t>(stream), use_graph);
+    return run_streamed(pl, p, s, use_graph);
 }
 
 kpp_status kpp_read_status(const void *workspace, kpp_stream_t stream)

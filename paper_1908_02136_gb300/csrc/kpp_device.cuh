@@ -19,14 +19,16 @@ constexpr int kWarp = 32;
 // Workspace control block (first 256 bytes of every workspace).
 // ---------------------------------------------------------------------------
 struct Control {
-    int32_t status;     // kpp_status written by the device (0 = OK)
-    uint32_t ticket;    // streamed form: CTAs finished with the current pass
-    uint32_t bar_count; // persistent form: grid barrier arrivals
-    uint32_t bar_gen;   // persistent form: grid barrier generation
-    int64_t pick;       // index drawn by the last pass (published to all CTAs)
-    uint32_t timeout_where;
-    uint32_t pad_[57];
+    int32_t status;          // kpp_status written by the device (0 = OK)
+    uint32_t ticket;         // streamed form: CTAs finished with the current pass
+    unsigned long long mail; // persistent form: (drawn index << 32) | (pass + 1)
+    uint32_t timeout_where;  // persistent form: pass whose wait gave up
+    uint32_t pad_[59];
 };
+
+// One tagged block sum per 32-byte slot, so the slots polled by every CTA
+// sit in different sectors.
+constexpr int kSlotWords = 4;
 static_assert(sizeof(Control) == 256, "control block is 256 bytes");
 
 // Everything a seeding kernel needs about one problem.
@@ -41,12 +43,16 @@ struct Problem {
     const int64_t *forced;
     int32_t n_forced;
     int32_t nblocks; // number of contiguous row blocks (one per CTA)
+    int32_t nseg;    // segments per block (one per warp)
     int64_t chunk;   // rows per block (last block may be shorter)
+    int64_t sw;      // rows per warp super-iteration; segments are whole ones
     int64_t *idx;
     float *d2;
     double *phi;
     Control *ctl;
-    double *block_sums; // [nblocks]
+    float2 *block_sums; // streamed form: [nblocks] pair sums of the pass
+    float2 *seg_sums;   // streamed form: [nblocks * nseg] pair sums of the pass
+    unsigned long long *slots; // persistent form: [2][nblocks * kSlotWords] tagged block sums
 };
 
 // ---------------------------------------------------------------------------
@@ -131,11 +137,11 @@ __device__ __forceinline__ void unpack_e4m3x2(uint32_t w16, float &lo, float &hi
     hi = f.y;
 }
 
-// Decode one 16-byte vector into Fmt<DT>::per16 floats.  For FP8 the value
-// is scale * decode(q), rounded once to FP32 (never fused into a later
-// subtraction, so a point and the same point used as a centre decode alike).
+// Decode one 16-byte vector into Fmt<DT>::per16 floats.  FP32 and BF16 give
+// the stored values exactly; FP8 gives the unscaled E4M3 values q (exact in
+// FP32) -- the row scale is applied inside the distance (see diff_fp8).
 template <int DT>
-__device__ __forceinline__ void decode16(uint4 v, float scale, float *out)
+__device__ __forceinline__ void decode16(uint4 v, float *out)
 {
     const uint32_t w[4] = {v.x, v.y, v.z, v.w};
     if constexpr (DT == KPP_F32) {
@@ -152,15 +158,12 @@ __device__ __forceinline__ void decode16(uint4 v, float scale, float *out)
             unpack_e4m3x2(w[i], out[4 * i], out[4 * i + 1]);
             unpack_e4m3x2(w[i] >> 16, out[4 * i + 2], out[4 * i + 3]);
         }
-#pragma unroll
-        for (int i = 0; i < 16; ++i)
-            out[i] = __fmul_rn(scale, out[i]);
     }
 }
 
-// Decode a single stored element (generic / scalar paths).
+// Decode a single stored element (generic / scalar paths); FP8 unscaled.
 template <int DT>
-__device__ __forceinline__ float decode1(const void *points, int64_t k, float scale)
+__device__ __forceinline__ float decode1(const void *points, int64_t k)
 {
     if constexpr (DT == KPP_F32) {
         return __ldg(reinterpret_cast<const float *>(points) + k);
@@ -171,16 +174,36 @@ __device__ __forceinline__ float decode1(const void *points, int64_t k, float sc
         uint8_t q = __ldg(reinterpret_cast<const unsigned char *>(points) + k);
         float lo, hi;
         unpack_e4m3x2(q, lo, hi);
-        return __fmul_rn(scale, lo);
+        return lo;
     }
 }
 
+// An FP8 centre coordinate c = s_c * q_c (exact in FP64, not in FP32) is held
+// as an unevaluated pair c_hi + c_lo with c_hi = RN(s_c * q_c) and c_lo the
+// exact rounding error.  A point coordinate x = s * q then differs from it by
+//   x - c = fma(s, q, -c_hi) - c_lo,
+// rounded about once relative to the difference itself, so cancellation near
+// the centre costs no accuracy and the centre's own distance is exactly 0.
+__device__ __forceinline__ void split_fp8_centre(float s, float q, float &hi, float &lo)
+{
+    hi = __fmul_rn(s, q);
+    lo = __fmaf_rn(s, q, -hi);
+}
+
+__device__ __forceinline__ float diff_fp8(float s, float q, float c_hi, float c_lo)
+{
+    return __fsub_rn(__fmaf_rn(s, q, -c_hi), c_lo);
+}
+
 // ---------------------------------------------------------------------------
-// FP32 two-sum accumulator: hi + lo equals the exact running sum up to
-// rounding in lo (Knuth's TwoSum, 6 flops, no FP64 on the per-row path).
+// FP32 two-sum pairs: hi + lo holds a running sum with about 48 significant
+// bits (Knuth's error-free TwoSum), so D^2 sums need no FP64 on the per-row
+// path (GB300's FP64 rate is a small fraction of its FP32 rate).  Integer
+// sums are exact while the error terms stay below 2^24.
 // ---------------------------------------------------------------------------
-struct Acc2 {
-    float hi = 0.f, lo = 0.f;
+struct Pair {
+    float hi, lo; // trivial type (usable in shared memory); value-initialise with Pair{}
+
     __device__ __forceinline__ void add(float x)
     {
         float s = __fadd_rn(hi, x);
@@ -189,8 +212,307 @@ struct Acc2 {
         hi = s;
         lo = __fadd_rn(lo, err);
     }
+    // pair + pair; the exact error term makes this commutative, so butterfly
+    // reductions leave the same value on every lane
+    __device__ __forceinline__ void add(const Pair &o)
+    {
+        float s = __fadd_rn(hi, o.hi);
+        float bb = __fsub_rn(s, hi);
+        float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(o.hi, bb));
+        hi = s;
+        lo = __fadd_rn(__fadd_rn(lo, o.lo), err);
+    }
     __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
 };
+
+// Butterfly sum of a pair over the 32 lanes (same result on every lane).
+__device__ __forceinline__ Pair warp_pair_sum(Pair p)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        Pair q;
+        q.hi = __shfl_xor_sync(0xffffffffu, p.hi, o);
+        q.lo = __shfl_xor_sync(0xffffffffu, p.lo, o);
+        p.add(q);
+    }
+    return p;
+}
+
+__device__ __forceinline__ Pair shfl_pair(Pair p, int src)
+{
+    Pair q;
+    q.hi = __shfl_sync(0xffffffffu, p.hi, src);
+    q.lo = __shfl_sync(0xffffffffu, p.lo, src);
+    return q;
+}
+
+__device__ __forceinline__ Pair pair_sum(Pair a, const Pair &b)
+{
+    a.add(b);
+    return a;
+}
+
+// Inclusive prefix over lanes (Hillis-Steele); `excl` gets the exclusive one.
+__device__ __forceinline__ Pair warp_pair_scan(Pair v, Pair &excl)
+{
+    const int lane = threadIdx.x & 31;
+    Pair incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        Pair y;
+        y.hi = __shfl_up_sync(0xffffffffu, incl.hi, o);
+        y.lo = __shfl_up_sync(0xffffffffu, incl.lo, o);
+        if (lane >= o) {
+            y.add(incl); // y precedes incl: keep the order of association
+            incl = y;
+        }
+    }
+    Pair e;
+    e.hi = __shfl_up_sync(0xffffffffu, incl.hi, 1);
+    e.lo = __shfl_up_sync(0xffffffffu, incl.lo, 1);
+    excl = lane ? e : Pair{};
+    return incl;
+}
+
+// ---------------------------------------------------------------------------
+// Warp-level inverse-CDF search (the draw), FP32 two-sum pairs throughout
+// and FP64 only where a decision is taken: t = u * T and the comparisons
+// "prefix > t", which are exact (a pair converts to FP64 exactly whenever its
+// parts are integers, as they are for integer coordinates).
+//
+// Over n values v_k >= 0 (get(k) returns a Pair): lane l sums the contiguous
+// slice [l*per, (l+1)*per) in order; the slice sums are prefix-summed over
+// lanes; the first lane whose running total exceeds t is walked element by
+// element, one element per lane.  The result is the first k with v_k > 0 and
+// base + prefix_k > t, where t = u * (base + total) in `u_mode`, else t =
+// u_or_t.  Every lane returns the same result.  n <= 1024.
+// ---------------------------------------------------------------------------
+struct PFind {
+    int64_t index;         // first crossing, or -1
+    int64_t last_positive; // largest k with v_k > 0, or -1
+    Pair before;           // base + prefix before the crossing
+    Pair total;            // base + sum of all values
+    double t;              // the threshold used
+};
+
+__device__ __forceinline__ bool pair_gt(const Pair &p, double t)
+{
+    return (double)p.hi + (double)p.lo > t;
+}
+
+template <class Get>
+__device__ __forceinline__ PFind warp_pfind(int n, Get get, Pair base, double u_or_t, bool u_mode)
+{
+    const int lane = threadIdx.x & 31;
+    const int per = (n + 31) >> 5;
+    const int b = lane * per;
+    const int e = b + per < n ? b + per : n;
+    Pair own{};
+    int lastpos = -1;
+    for (int k = b; k < e; ++k) {
+        const Pair v = get(k);
+        own.add(v);
+        if (v.hi > 0.f)
+            lastpos = k;
+    }
+    Pair excl;
+    const Pair incl = warp_pair_scan(own, excl);
+    PFind r;
+    r.before = Pair{};
+    r.total = pair_sum(base, shfl_pair(incl, 31));
+    r.t = u_mode ? u_or_t * ((double)r.total.hi + (double)r.total.lo) : u_or_t;
+    const unsigned cross = __ballot_sync(0xffffffffu, b < e && pair_gt(pair_sum(base, incl), r.t));
+    r.index = -1;
+    if (cross) {
+        const int L = __ffs(cross) - 1;
+        const Pair start = pair_sum(base, shfl_pair(excl, L));
+        const int k = L * per + lane;
+        const bool in = lane < per && k < n;
+        const Pair v = in ? get(k) : Pair{};
+        Pair vex;
+        const Pair vin = warp_pair_scan(v, vex);
+        const bool hit = in && v.hi > 0.f && pair_gt(pair_sum(start, vin), r.t);
+        const unsigned h = __ballot_sync(0xffffffffu, hit);
+        // rounding can leave the slice's own walk short of t: then its last
+        // point with weight
+        const unsigned pos = __ballot_sync(0xffffffffu, in && v.hi > 0.f);
+        const int j = h ? __ffs(h) - 1 : (pos ? 31 - __clz(pos) : -1);
+        if (j >= 0) {
+            r.index = L * per + j;
+            r.before = pair_sum(start, shfl_pair(vex, j));
+        }
+    }
+    int lp = lastpos;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const int y = __shfl_xor_sync(0xffffffffu, lp, o);
+        lp = y > lp ? y : lp;
+    }
+    r.last_positive = lp;
+    return r;
+}
+
+// Rows [first, last) of segment `seg` of a block of `rows` rows starting at
+// `row0`: the block's super-iterations of `sw` rows are split evenly over
+// `nseg` segments, segment w taking [w * ns / nseg, (w + 1) * ns / nseg).
+__host__ __device__ __forceinline__ void segment_rows(int64_t row0, int64_t rows, int64_t sw,
+                                                      int nseg, int seg, int64_t *first,
+                                                      int64_t *last)
+{
+    const int64_t ns = (rows + sw - 1) / sw;
+    const int64_t sb = (int64_t)seg * ns / nseg, se = (int64_t)(seg + 1) * ns / nseg;
+    *first = row0 + sb * sw;
+    const int64_t e = row0 + se * sw;
+    *last = e < row0 + rows ? e : row0 + rows;
+}
+
+constexpr int kStage = 1024; // values staged in shared memory per round
+
+// Shared state of block_rows_find.
+struct RowsShared {
+    int64_t found;
+    int64_t last_positive;
+    Pair total;
+};
+
+// Point-level search of a draw over rows [first, last) whose D^2 are read by
+// `get_d2(row)`, in rounds of kStage rows staged in shared memory by the whole
+// block and scanned by warp 0, from prefix `base` against threshold t (+inf:
+// take the last row with weight).  All threads must call it; all return the
+// row (`first` if no row has weight).  `*before` gets the prefix before it.
+template <class GetD2>
+__device__ int64_t block_rows_find(int64_t first, int64_t last, GetD2 get_d2, Pair base, double t,
+                                   float *stage, RowsShared *sh, Pair *before = nullptr)
+{
+    int64_t lastpos = -1;
+    Pair lastpos_before{};
+    for (int64_t w0 = first; w0 < last; w0 += kStage) {
+        const int cnt = (int)((last - w0) < kStage ? (last - w0) : kStage);
+        __syncthreads();
+        for (int k = threadIdx.x; k < cnt; k += blockDim.x)
+            stage[k] = get_d2(w0 + k);
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            const PFind r = warp_pfind(
+                cnt, [&](int k) { return Pair{stage[k], 0.f}; }, base, t, false);
+            if (threadIdx.x == 0) {
+                sh->found = r.index >= 0 ? w0 + r.index : -1;
+                sh->last_positive = r.last_positive >= 0 ? w0 + r.last_positive : -1;
+                sh->total = r.index >= 0 ? r.before : r.total;
+            }
+        }
+        __syncthreads();
+        const int64_t f = sh->found, lp = sh->last_positive;
+        const Pair tot = sh->total;
+        if (f >= 0) {
+            if (before)
+                *before = tot;
+            __syncthreads();
+            return f;
+        }
+        if (lp >= 0) {
+            lastpos = lp;
+            lastpos_before = base; // prefix at the start of that round
+        }
+        base = tot;
+    }
+    __syncthreads();
+    if (before)
+        *before = lastpos_before;
+    return lastpos >= 0 ? lastpos : first;
+}
+
+// ---------------------------------------------------------------------------
+// Tagged words for the persistent form's grid-wide exchange.  Every exchanged
+// value fits one 64-bit word, written and read with single-copy-atomic
+// relaxed accesses, and carries its own pass tag, so a reader needs no fence:
+//   block-sum slot:  (bits(lo) << 32) | bits(hi) with the sign bit of hi
+//                    (hi >= 0) replaced by the tag of the pass;
+//   mailbox:         (index << 32) | (pass + 1).
+// The slot of pass m lives in buffer m & 1, and its tag bit is
+// ((m >> 1) + 1) & 1: it flips between two uses of the same buffer, and a
+// zeroed buffer never matches the first use.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t slot_tag(int m) { return (uint32_t)(((m >> 1) + 1) & 1); }
+
+__device__ __forceinline__ unsigned long long pack_slot(const Pair &p, int m)
+{
+    const uint32_t hi = (__float_as_uint(p.hi) & 0x7fffffffu) | (slot_tag(m) << 31);
+    return ((unsigned long long)__float_as_uint(p.lo) << 32) | hi;
+}
+
+__device__ __forceinline__ Pair unpack_slot(unsigned long long w)
+{
+    return Pair{__uint_as_float((uint32_t)w & 0x7fffffffu), __uint_as_float((uint32_t)(w >> 32))};
+}
+
+__device__ __forceinline__ void st_relaxed_u64(unsigned long long *a, unsigned long long v)
+{
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(a), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long *a)
+{
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(a) : "memory");
+    return v;
+}
+
+// ---------------------------------------------------------------------------
+// Bounded waits (persistent form, cooperative launch only).  A wait that
+// outlasts its deadline records KPP_ERR_TIMEOUT (and the pass) in the status
+// word and returns false instead of hanging; any other error recorded by
+// another CTA also ends the wait.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ bool give_up(Control *ctl, uint64_t t0, uint64_t timeout_ns,
+                                        uint32_t it, uint32_t where)
+{
+    if ((it & 63u) == 0 && *(volatile int32_t *)&ctl->status != KPP_OK)
+        return true;
+    if (global_ns() - t0 > timeout_ns) {
+        if (atomicCAS(&ctl->status, KPP_OK, KPP_ERR_TIMEOUT) == KPP_OK)
+            ctl->timeout_where = where;
+        return true;
+    }
+    return false;
+}
+
+// Waits until slot `a` carries the tag of pass m; returns false on give-up.
+__device__ __forceinline__ bool wait_slot(const unsigned long long *a, int m, Control *ctl,
+                                          uint64_t timeout_ns, Pair *out)
+{
+    const uint32_t tag = slot_tag(m);
+    const uint64_t t0 = global_ns();
+    for (uint32_t it = 1;; ++it) {
+        const unsigned long long w = ld_relaxed_u64(a);
+        if (((uint32_t)w >> 31) == tag) {
+            *out = unpack_slot(w);
+            return true;
+        }
+        if (give_up(ctl, t0, timeout_ns, it, (uint32_t)m))
+            return false;
+    }
+}
+
+// Waits until the mailbox carries pass m's index; returns it, or -1.
+__device__ __forceinline__ int64_t wait_mail(Control *ctl, int m, uint64_t timeout_ns)
+{
+    const uint64_t t0 = global_ns();
+    for (uint32_t it = 1;; ++it) {
+        const unsigned long long w = ld_relaxed_u64(&ctl->mail);
+        if ((uint32_t)w == (uint32_t)(m + 1))
+            return (int64_t)(w >> 32);
+        if (give_up(ctl, t0, timeout_ns, it, (uint32_t)m))
+            return -1;
+    }
+}
 
 // ---------------------------------------------------------------------------
 // Block reductions and scans (deterministic association).
@@ -219,174 +541,6 @@ __device__ __forceinline__ double block_sum(double v, double *sh)
     for (int w = 0; w < NT / 32; ++w)
         t += sh[w];
     return t;
-}
-
-// Exclusive prefix of one double per thread, in thread order; also returns
-// the total.  `sh` needs NT/32 + 1 doubles.
-template <int NT>
-__device__ __forceinline__ double block_exclusive_scan(double v, double *sh, double &total)
-{
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    double incl = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        double y = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o)
-            incl += y;
-    }
-    double prev = __shfl_up_sync(0xffffffffu, incl, 1);
-    __syncthreads();
-    if (lane == 31)
-        sh[warp] = incl;
-    __syncthreads();
-    double before = 0.0, all = 0.0;
-#pragma unroll
-    for (int w = 0; w < NT / 32; ++w) {
-        if (w < warp)
-            before += sh[w];
-        all += sh[w];
-    }
-    total = all;
-    return lane ? before + prev : before;
-}
-
-template <int NT>
-__device__ __forceinline__ int64_t block_min_i64(int64_t v, int64_t *sh)
-{
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        int64_t y = __shfl_xor_sync(0xffffffffu, v, o);
-        v = y < v ? y : v;
-    }
-    __syncthreads();
-    if (lane == 0)
-        sh[warp] = v;
-    __syncthreads();
-    int64_t r = sh[0];
-#pragma unroll
-    for (int w = 1; w < NT / 32; ++w)
-        r = sh[w] < r ? sh[w] : r;
-    return r;
-}
-
-template <int NT>
-__device__ __forceinline__ int64_t block_max_i64(int64_t v, int64_t *sh)
-{
-    return -block_min_i64<NT>(-v, sh);
-}
-
-// Ordered FP64 total of n values: contiguous per-thread slices summed in
-// order, slice totals summed in thread order (the association block_find
-// uses for its total).
-template <int NT, class Get>
-__device__ double block_ordered_total(int64_t n, Get get, double *shd)
-{
-    const int64_t per = (n + NT - 1) / NT;
-    const int64_t b = (int64_t)threadIdx.x * per;
-    const int64_t e = b + per < n ? b + per : n;
-    double own = 0.0;
-    for (int64_t k = b; k < e; ++k)
-        own += get(k);
-    double total;
-    block_exclusive_scan<NT>(own, shd, total);
-    return total;
-}
-
-struct FindResult {
-    int64_t index;  // first k with base + prefix_k > t, or -1
-    double before;  // base + prefix up to k-1 (valid if index >= 0)
-    double total;   // base + sum of all n values
-    int64_t last_positive; // largest k with value > 0, or -1
-};
-
-// Block-cooperative inverse-CDF search over n values v_k = get(k):
-// thread t sums the contiguous slice [t*per, (t+1)*per) in order, slice
-// totals are prefix-summed in thread order, and every slice is walked again
-// from its exclusive prefix.  The threshold is t = u * (base + total) when
-// `u_mode` is set, else `u_or_t` itself.  All threads return the same result.
-template <int NT, class Get>
-__device__ FindResult block_find(int64_t n, Get get, double base, double u_or_t, bool u_mode,
-                                 double *shd, int64_t *shi, double *t_out = nullptr)
-{
-    const int64_t per = (n + NT - 1) / NT;
-    const int64_t b = (int64_t)threadIdx.x * per;
-    const int64_t e = b + per < n ? b + per : n;
-    double own = 0.0;
-    int64_t lastpos = -1;
-    for (int64_t k = b; k < e; ++k) {
-        double v = get(k);
-        own += v;
-        if (v > 0.0)
-            lastpos = k;
-    }
-    double total;
-    double excl = block_exclusive_scan<NT>(own, shd, total);
-    const double t = u_mode ? u_or_t * (base + total) : u_or_t;
-    if (t_out)
-        *t_out = t;
-    double run = base + excl;
-    int64_t cand = INT64_MAX;
-    double cand_before = 0.0;
-    // First crossing of t within the slice; a zero weight never crosses.
-    for (int64_t k = b; k < e; ++k) {
-        double v = get(k);
-        double next = run + v;
-        if (v > 0.0 && next > t) {
-            cand = k;
-            cand_before = run;
-            break;
-        }
-        run = next;
-    }
-    FindResult r;
-    r.total = base + total;
-    r.index = block_min_i64<NT>(cand, shi);
-    r.last_positive = block_max_i64<NT>(lastpos, shi);
-    __syncthreads();
-    if (cand == r.index && cand != INT64_MAX)
-        shd[0] = cand_before;
-    __syncthreads();
-    r.before = shd[0];
-    if (r.index == INT64_MAX)
-        r.index = -1;
-    __syncthreads();
-    return r;
-}
-
-// The draw of seed m (m >= 1) from per-block FP64 sums and per-point FP32
-// D^2, by one thread block: find the block whose running FP64 sum first
-// exceeds t = u_m * T, then rescan only that block's points from the
-// block's exclusive prefix.  Returns the drawn index, or -1 if T == 0
-// (degenerate).  `T_out` gets T on all threads.
-template <int NT>
-__device__ int64_t hierarchical_draw(const double *block_sums, int nblocks, const float *d2,
-                                     int64_t N, int64_t chunk, double u, double *shd,
-                                     int64_t *shi, double *T_out)
-{
-    double t;
-    FindResult r1 = block_find<NT>(
-        nblocks, [&](int64_t k) { return ld_cg(block_sums + k); }, 0.0, u, true, shd, shi, &t);
-    *T_out = r1.total;
-    if (!(r1.total > 0.0))
-        return -1;
-    int64_t blk = r1.index;
-    double base = r1.before;
-    double thr = t;
-    if (blk < 0) { // rounding left no block above t: last block with weight
-        blk = r1.last_positive;
-        thr = INFINITY;
-        base = 0.0;
-    }
-    const int64_t row0 = blk * chunk;
-    const int64_t n2 = (N - row0) < chunk ? (N - row0) : chunk;
-    FindResult r2 = block_find<NT>(
-        n2, [&](int64_t k) { return (double)ld_cg(d2 + row0 + k); }, base, thr, false, shd, shi);
-    if (r2.index >= 0)
-        return row0 + r2.index;
-    // rounding inside the block: its last point with weight (one exists,
-    // since the block's sum is positive)
-    return row0 + (r2.last_positive >= 0 ? r2.last_positive : 0);
 }
 
 } // namespace kpp

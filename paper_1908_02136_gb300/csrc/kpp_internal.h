@@ -18,8 +18,32 @@ struct StreamedKernel {
 
 bool streamed_lookup(int dt, int d, int lanes, StreamedKernel *out);
 int streamed_threads();
+int streamed_segments();
+size_t streamed_smem(const StreamedKernel &k, int d);
 cudaError_t streamed_launch(const StreamedKernel &k, int grid, const Problem &p, int m,
                             cudaStream_t stream);
+
+// Runtime arguments of the persistent kernel.
+struct PersistArgs {
+    int64_t cache_supers; // super-iterations of each warp's segment kept in smem
+    int32_t reverse;     // walk rows backwards on odd passes
+    int32_t l2_hint;     // global point loads: 0 none, 1 evict_last, 2 evict_first
+    uint64_t timeout_ns; // bound of every grid-barrier wait
+};
+
+struct PersistentKernel {
+    const void *fn_smem;   // D^2 in shared memory
+    const void *fn_global; // D^2 in the output array
+    int rows_align;          // rows per super-iteration; blocks are multiples of it
+    int row_bytes;
+    int lanes;
+};
+
+bool persistent_lookup(int dt, int d, int lanes, PersistentKernel *out);
+int persistent_threads();
+int persistent_segments();
+cudaError_t persistent_launch(const void *fn, int grid, size_t smem, const Problem &p,
+                              const PersistArgs &a, cudaStream_t stream);
 
 } // namespace kpp
 

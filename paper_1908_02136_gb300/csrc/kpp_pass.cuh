@@ -1,9 +1,12 @@
 // kpp_pass.cuh -- the per-point work of one seeding pass, shared by the
-// streamed and persistent forms: distance of every point of a contiguous
-// row range to the newest centre (difference form, FP32 FMA), in-place
-// min-update of D^2, and the range's D^2 sum (FP32 two-sum per lane, FP64
-// across lanes).  Algorithm 1/2: d_{m,l} = d(H_m, n_l), d_sn = min over
-// seeds of the squared distance.
+// streamed and persistent forms (Algorithm 2: the per-point loop run in
+// parallel over contiguous partitions of the points):
+//   - distance of every point of the CTA's row range to the newest centre,
+//     d_{m,l} = d(H_m, n_l), in the difference form with FP32 FMAs;
+//   - the min-update of the nearest squared distance d_sn (D^2);
+//   - the D^2 sum of each warp's contiguous segment of rows, accumulated per
+//     lane as FP32 two-sum pairs and reduced across the warp once per pass,
+//     and the CTA's sum of its segments.
 #pragma once
 
 #include "kpp_device.cuh"
@@ -16,6 +19,7 @@ namespace kpp {
 //     lane (g, l) ends up owning row base + l * (32 / L) + g.
 //   Narrow rows (< 16 bytes): one 16-byte vector holds RPV whole rows; a
 //     lane owns RPV consecutive rows and a warp covers 32 * RPV rows.
+// Each warp walks a contiguous run of super-iterations (its segment).
 template <int DT, int D, int L_>
 struct Geom {
     static constexpr int EB = Fmt<DT>::bytes;
@@ -37,11 +41,22 @@ struct Geom {
     static_assert(!WIDE || (L % JB == 0), "slot batches tile the slots");
 };
 
-// Per-lane slice of the newest centre, decoded to FP32 once per pass.
+// Per-lane slice of the newest centre, decoded to FP32 once per pass.  For
+// FP8 each coordinate is the pair (c_hi, c_lo) of split_fp8_centre.
 template <int DT, int D, int L_>
 struct CentreRegs {
     using G = Geom<DT, D, L_>;
+    static constexpr int NLO = (DT == KPP_FP8_E4M3) ? G::CREG : 1;
     float c[G::CREG];
+    float clo[NLO];
+
+    __device__ __forceinline__ void set(int k, float s, float raw)
+    {
+        if constexpr (DT == KPP_FP8_E4M3)
+            split_fp8_centre(s, raw, c[k], clo[k]);
+        else
+            c[k] = raw;
+    }
 
     __device__ __forceinline__ void load(const void *points, const float *scales, int64_t ci)
     {
@@ -53,38 +68,144 @@ struct CentreRegs {
 #pragma unroll
             for (int v = 0; v < G::VPL; ++v) {
                 uint4 x = *reinterpret_cast<const uint4 *>(row + (v * G::L + l) * 16);
-                decode16<DT>(x, sc, c + v * G::EPV);
+                float f[G::EPV];
+                decode16<DT>(x, f);
+#pragma unroll
+                for (int e = 0; e < G::EPV; ++e)
+                    set(v * G::EPV + e, sc, f[e]);
             }
         } else {
             float tmp[D];
 #pragma unroll
             for (int k = 0; k < D; ++k)
-                tmp[k] = decode1<DT>(points, ci * D + k, sc);
+                tmp[k] = decode1<DT>(points, ci * D + k);
 #pragma unroll
             for (int e = 0; e < G::EPV; ++e)
-                c[e] = tmp[e % D];
+                set(e, sc, tmp[e % D]);
+        }
+    }
+
+    // Adds sum_e (x_e - c_{k0+e})^2 of one decoded vector into (a0, a1).
+    // `s` is the row scale (FP8 only).
+    template <int N>
+    __device__ __forceinline__ void accum(const float *f, int k0, float s, float &a0,
+                                          float &a1) const
+    {
+#pragma unroll
+        for (int e = 0; e < N; e += 2) {
+            float t0, t1;
+            if constexpr (DT == KPP_FP8_E4M3) {
+                t0 = diff_fp8(s, f[e], c[k0 + e], clo[k0 + e]);
+                t1 = diff_fp8(s, f[e + 1], c[k0 + e + 1], clo[k0 + e + 1]);
+            } else {
+                t0 = f[e] - c[k0 + e];
+                t1 = f[e + 1] - c[k0 + e + 1];
+            }
+            a0 = fmaf(t0, t0, a0);
+            a1 = fmaf(t1, t1, a1);
         }
     }
 };
 
-// One pass over rows [row_begin, row_end) by all warps of the CTA.
-// m == 0 writes D^2 (the initial infinity makes the min a plain store);
-// m > 0 stores only where D^2 decreases.  Returns this thread's share of
-// the range's D^2 sum.
-template <int DT, int D, int L_>
-__device__ __forceinline__ Acc2 pass_rows(const void *points, const float *scales, float *d2,
-                                          int64_t row_begin, int64_t row_end, bool first_pass,
-                                          const CentreRegs<DT, D, L_> &cr)
+// Where D^2 lives during a pass.
+enum D2Mode {
+    D2_INPLACE = 0, // the global D^2 array, read and written in place
+    D2_SMEM = 1     // shared memory (copied out to the global array when asked)
+};
+
+struct PassIO {
+    int64_t r0, r1;        // this CTA's rows
+    bool first;            // pass 0: D^2 starts at +infinity
+    bool reverse;          // walk each segment last super-iteration first
+    const char *gpts;      // points in global memory
+    const float *scales;   // FP8 row scales
+    char *cache;           // shared-memory copy of the first `cache_supers`
+    int64_t cache_supers;  //   super-iterations of every warp's segment, or null
+    bool fill_cache;       // this pass loads the cached rows and stores them
+    float *d2;             // D2_INPLACE: the global D^2 array
+    float *d2_out;         // D2_SMEM: also store this pass's D^2 here, or null
+    float *d2s;            // D2_SMEM: shared memory, indexed by row - r0
+    float2 *segs;          // segment sums of this CTA, one per warp (global or smem)
+    uint64_t policy;       // L2 cache policy of global point loads (0: none)
+};
+
+__device__ __forceinline__ uint4 ld_global_hint(const void *ptr, uint64_t policy)
+{
+    uint4 v;
+    asm volatile(
+        "ld.global.nc.L1::no_allocate.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
+        : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+        : "l"(ptr), "l"(policy));
+    return v;
+}
+
+__device__ __forceinline__ uint64_t policy_evict_last()
+{
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+__device__ __forceinline__ uint64_t policy_evict_first()
+{
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+// One 16-byte vector of row data: from the shared-memory cache slot of the
+// super-iteration (if cached and not being filled), else from global memory.
+__device__ __forceinline__ uint4 load_vec(const PassIO &io, const char *cslot, int64_t rb,
+                                          int64_t row, int byte_in_row, int RB)
+{
+    if (cslot)
+        return *reinterpret_cast<const uint4 *>(cslot + (row - rb) * RB + byte_in_row);
+    const char *g = io.gpts + row * RB + byte_in_row;
+    return io.policy ? ld_global_hint(g, io.policy) : ld_stream16(g);
+}
+
+// min-update of one owned row; returns the row's new D^2.
+template <int MODE>
+__device__ __forceinline__ float update_d2(const PassIO &io, int64_t row, float v)
+{
+    float *slot = (MODE == D2_INPLACE) ? io.d2 + row : io.d2s + (row - io.r0);
+    if (io.first) {
+        *slot = v;
+    } else {
+        const float old = *slot;
+        if (v < old)
+            *slot = v;
+        else
+            v = old;
+    }
+    if (MODE == D2_SMEM && io.d2_out)
+        io.d2_out[row] = v;
+    return v;
+}
+
+// One pass over rows [r0, r1) by all warps of the CTA, each over its own
+// segment.  Writes the warp's segment sum and returns it (identical on all
+// lanes of the warp).
+template <int DT, int D, int L_, int MODE>
+__device__ __forceinline__ Pair pass_rows(const PassIO &io, const CentreRegs<DT, D, L_> &cr)
 {
     using G = Geom<DT, D, L_>;
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int nwarps = blockDim.x >> 5;
-    const char *base_ptr = reinterpret_cast<const char *>(points);
-    Acc2 acc;
+    int64_t seg_first, seg_last;
+    segment_rows(io.r0, io.r1 - io.r0, G::SW, nwarps, warp, &seg_first, &seg_last);
+    const int64_t nsup = (seg_last - seg_first + G::SW - 1) / G::SW;
+    Pair lacc{};
 
-    for (int64_t rb = row_begin + (int64_t)warp * G::SW; rb < row_end;
-         rb += (int64_t)nwarps * G::SW) {
+    for (int64_t j = 0; j < nsup; ++j) {
+        const int64_t jj = io.reverse ? (nsup - 1 - j) : j;
+        const int64_t rb = seg_first + jj * G::SW;
+        char *slot = (io.cache != nullptr && jj < io.cache_supers)
+                         ? io.cache + ((int64_t)warp * io.cache_supers + jj) * G::SW * G::RB
+                         : nullptr;
+        const char *from = io.fill_cache ? nullptr : slot;
+        char *store = io.fill_cache ? slot : nullptr;
         float mine[G::RPV];
         int64_t own_row;
         if constexpr (G::WIDE) {
@@ -95,35 +216,41 @@ __device__ __forceinline__ Acc2 pass_rows(const void *points, const float *scale
                 uint4 x[G::JB][G::VPL];
                 float sc[G::JB];
 #pragma unroll
-                for (int jj = 0; jj < G::JB; ++jj) {
-                    const int64_t row = rb + (int64_t)(jb + jj) * (32 / G::L) + g;
-                    const bool ok = row < row_end;
-                    sc[jj] = (DT == KPP_FP8_E4M3 && ok) ? __ldg(scales + row) : 1.0f;
+                for (int q = 0; q < G::JB; ++q) {
+                    const int64_t row = rb + (int64_t)(jb + q) * (32 / G::L) + g;
+                    const bool ok = row < seg_last;
+                    sc[q] = (DT == KPP_FP8_E4M3 && ok) ? __ldg(io.scales + row) : 1.0f;
 #pragma unroll
                     for (int v = 0; v < G::VPL; ++v)
-                        x[jj][v] = ok ? ld_stream16(base_ptr + row * G::RB + (v * G::L + l) * 16)
-                                      : make_uint4(0, 0, 0, 0);
+                        x[q][v] = ok ? load_vec(io, from, rb, row, (v * G::L + l) * 16, G::RB)
+                                     : make_uint4(0, 0, 0, 0);
+                }
+                if (store) {
+#pragma unroll
+                    for (int q = 0; q < G::JB; ++q) {
+                        const int64_t row = rb + (int64_t)(jb + q) * (32 / G::L) + g;
+                        if (row < seg_last) {
+#pragma unroll
+                            for (int v = 0; v < G::VPL; ++v)
+                                *reinterpret_cast<uint4 *>(store + (row - rb) * G::RB +
+                                                           (v * G::L + l) * 16) = x[q][v];
+                        }
+                    }
                 }
 #pragma unroll
-                for (int jj = 0; jj < G::JB; ++jj) {
+                for (int q = 0; q < G::JB; ++q) {
                     float a0 = 0.f, a1 = 0.f;
 #pragma unroll
                     for (int v = 0; v < G::VPL; ++v) {
                         float f[G::EPV];
-                        decode16<DT>(x[jj][v], sc[jj], f);
-#pragma unroll
-                        for (int e = 0; e < G::EPV; e += 2) {
-                            float t0 = f[e] - cr.c[v * G::EPV + e];
-                            float t1 = f[e + 1] - cr.c[v * G::EPV + e + 1];
-                            a0 = fmaf(t0, t0, a0);
-                            a1 = fmaf(t1, t1, a1);
-                        }
+                        decode16<DT>(x[q][v], f);
+                        cr.template accum<G::EPV>(f, v * G::EPV, sc[q], a0, a1);
                     }
                     float part = a0 + a1;
 #pragma unroll
                     for (int o = G::L / 2; o > 0; o >>= 1)
                         part += __shfl_xor_sync(0xffffffffu, part, o);
-                    if (l == jb + jj)
+                    if (l == jb + q)
                         mine[0] = part;
                 }
             }
@@ -131,98 +258,111 @@ __device__ __forceinline__ Acc2 pass_rows(const void *points, const float *scale
         } else {
             own_row = rb + (int64_t)lane * G::RPV;
             float f[G::EPV];
-            if (own_row + G::RPV <= row_end) {
-                uint4 x = ld_stream16(base_ptr + own_row * G::RB);
-                decode16<DT>(x, 1.0f, f);
-                if constexpr (DT == KPP_FP8_E4M3) {
+            float sc[G::RPV];
+            if (own_row + G::RPV <= seg_last) {
+                uint4 x = load_vec(io, from, rb, own_row, 0, G::RB);
+                if (store)
+                    *reinterpret_cast<uint4 *>(store + (own_row - rb) * G::RB) = x;
+                decode16<DT>(x, f);
 #pragma unroll
-                    for (int r = 0; r < G::RPV; ++r) {
-                        const float s = __ldg(scales + own_row + r);
-#pragma unroll
-                        for (int k = 0; k < D; ++k)
-                            f[r * D + k] = __fmul_rn(s, f[r * D + k]);
-                    }
-                }
+                for (int r = 0; r < G::RPV; ++r)
+                    sc[r] = (DT == KPP_FP8_E4M3) ? __ldg(io.scales + own_row + r) : 1.0f;
             } else {
-                // ragged tail: element loads, never past row_end
+                // ragged tail of the segment: element loads from global memory,
+                // never past its end (the cache is not used for these rows)
 #pragma unroll
                 for (int r = 0; r < G::RPV; ++r) {
                     const int64_t row = own_row + r;
-                    const float s = (DT == KPP_FP8_E4M3 && row < row_end) ? __ldg(scales + row) : 1.0f;
+                    const bool ok = row < seg_last;
+                    sc[r] = (DT == KPP_FP8_E4M3 && ok) ? __ldg(io.scales + row) : 1.0f;
 #pragma unroll
                     for (int k = 0; k < D; ++k)
-                        f[r * D + k] = row < row_end ? decode1<DT>(points, row * D + k, s) : 0.f;
+                        f[r * D + k] = ok ? decode1<DT>(io.gpts, row * D + k) : 0.f;
                 }
             }
 #pragma unroll
             for (int r = 0; r < G::RPV; ++r) {
-                float a = 0.f;
-#pragma unroll
-                for (int k = 0; k < D; ++k) {
-                    float t = f[r * D + k] - cr.c[r * D + k];
-                    a = fmaf(t, t, a);
-                }
-                mine[r] = a;
+                float a0 = 0.f, a1 = 0.f;
+                cr.template accum<D>(f + r * D, r * D, sc[r], a0, a1);
+                mine[r] = a0 + a1;
             }
         }
-        // min-update of the rows this lane owns, and their sum
 #pragma unroll
         for (int r = 0; r < G::RPV; ++r) {
             const int64_t row = own_row + r;
-            if (row < row_end) {
-                float v = mine[r];
-                if (first_pass) {
-                    d2[row] = v;
-                } else {
-                    const float old = d2[row];
-                    if (v < old)
-                        d2[row] = v;
-                    else
-                        v = old;
-                }
-                acc.add(v);
-            }
+            if (row < seg_last)
+                lacc.add(update_d2<MODE>(io, row, mine[r]));
         }
     }
-    return acc;
+    const Pair seg = warp_pair_sum(lacc);
+    if (lane == 0)
+        io.segs[warp] = make_float2(seg.hi, seg.lo);
+    return seg;
+}
+
+// The CTA's D^2 sum: warp pairs added in warp order, rounded once to FP64.
+// All threads return it.  `sh` holds 2 floats per warp.
+__device__ __forceinline__ double cta_sum(const Pair &wacc, float *sh)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) {
+        sh[2 * warp] = wacc.hi;
+        sh[2 * warp + 1] = wacc.lo;
+    }
+    __syncthreads();
+    Pair t{};
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+        Pair q;
+        q.hi = sh[2 * w];
+        q.lo = sh[2 * w + 1];
+        t.add(q);
+    }
+    return t.value();
 }
 
 // Generic pass for any d and any row alignment: one thread per row, element
-// loads, centre in shared memory (`c_sh`, d floats).  Used when no
-// specialisation for (dtype, d) is built.
+// loads, centre in shared memory (c_sh[0..d) = c_hi, c_sh[d..2d) = c_lo for
+// FP8).  Segments as in pass_rows with 32-row super-iterations.
 template <int DT>
-__device__ __forceinline__ Acc2 pass_rows_generic(const void *points, const float *scales,
-                                                  float *d2, int64_t row_begin, int64_t row_end,
-                                                  int d, bool first_pass, const float *c_sh)
+__device__ __forceinline__ Pair pass_rows_generic(const PassIO &io, int d, const float *c_sh)
 {
-    Acc2 acc;
-    for (int64_t row = row_begin + threadIdx.x; row < row_end; row += blockDim.x) {
-        const float s = (DT == KPP_FP8_E4M3) ? __ldg(scales + row) : 1.0f;
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int nwarps = blockDim.x >> 5;
+    int64_t seg_first, seg_last;
+    segment_rows(io.r0, io.r1 - io.r0, 32, nwarps, warp, &seg_first, &seg_last);
+    Pair lacc{};
+    for (int64_t row = seg_first + lane; row < seg_last; row += 32) {
+        const float sc = (DT == KPP_FP8_E4M3) ? __ldg(io.scales + row) : 1.0f;
         float a0 = 0.f, a1 = 0.f;
         int k = 0;
         for (; k + 1 < d; k += 2) {
-            float t0 = decode1<DT>(points, row * d + k, s) - c_sh[k];
-            float t1 = decode1<DT>(points, row * d + k + 1, s) - c_sh[k + 1];
+            float q0 = decode1<DT>(io.gpts, row * d + k);
+            float q1 = decode1<DT>(io.gpts, row * d + k + 1);
+            float t0, t1;
+            if constexpr (DT == KPP_FP8_E4M3) {
+                t0 = diff_fp8(sc, q0, c_sh[k], c_sh[d + k]);
+                t1 = diff_fp8(sc, q1, c_sh[k + 1], c_sh[d + k + 1]);
+            } else {
+                t0 = q0 - c_sh[k];
+                t1 = q1 - c_sh[k + 1];
+            }
             a0 = fmaf(t0, t0, a0);
             a1 = fmaf(t1, t1, a1);
         }
         if (k < d) {
-            float t0 = decode1<DT>(points, row * d + k, s) - c_sh[k];
+            float q0 = decode1<DT>(io.gpts, row * d + k);
+            float t0 = (DT == KPP_FP8_E4M3) ? diff_fp8(sc, q0, c_sh[k], c_sh[d + k])
+                                            : q0 - c_sh[k];
             a0 = fmaf(t0, t0, a0);
         }
-        float v = a0 + a1;
-        if (first_pass) {
-            d2[row] = v;
-        } else {
-            const float old = d2[row];
-            if (v < old)
-                d2[row] = v;
-            else
-                v = old;
-        }
-        acc.add(v);
+        lacc.add(update_d2<D2_INPLACE>(io, row, a0 + a1));
     }
-    return acc;
+    const Pair seg = warp_pair_sum(lacc);
+    if (lane == 0)
+        io.segs[warp] = make_float2(seg.hi, seg.lo);
+    return seg;
 }
 
 template <int DT>
@@ -230,8 +370,13 @@ __device__ __forceinline__ void load_centre_smem(const void *points, const float
                                                  int64_t ci, int d, float *c_sh)
 {
     const float s = (DT == KPP_FP8_E4M3) ? __ldg(scales + ci) : 1.0f;
-    for (int k = threadIdx.x; k < d; k += blockDim.x)
-        c_sh[k] = decode1<DT>(points, ci * d + k, s);
+    for (int k = threadIdx.x; k < d; k += blockDim.x) {
+        const float q = decode1<DT>(points, ci * d + k);
+        if constexpr (DT == KPP_FP8_E4M3)
+            split_fp8_centre(s, q, c_sh[k], c_sh[d + k]);
+        else
+            c_sh[k] = q;
+    }
 }
 
 } // namespace kpp

@@ -1,54 +1,18 @@
 // kpp_streamed.cu -- streamed form: one kernel launch per seeding pass.
 //
 // Launch m (m = 0..K-1) reads the centre index idx[m], streams every point
-// once (Algorithm 2: the per-point loop "in parallel", the points
-// partitioned into contiguous per-CTA ranges N_1..N_l), updates D^2 in HBM
-// and writes the CTA's FP64 D^2 sum.  The last CTA to finish (atomic
-// ticket) draws seed m+1 from the block sums and a rescan of the winning
-// block (the sum the paper takes with a double-precision Thrust reduction,
-// Section II, fused into the pass), and writes idx[m+1].  The K launches are
-// captured once into a CUDA graph by the host code.
+// once (Algorithm 2: the per-point loop in parallel over contiguous per-CTA
+// partitions N_1..N_l), updates D^2 in HBM, and writes per-warp-segment and
+// per-CTA D^2 sums.  The last CTA to finish (atomic ticket) draws seed m+1 --
+// block, then segment, then point -- and writes idx[m+1] (the sum the
+// paper takes with a double-precision Thrust reduction, Section II, fused
+// into the pass).  The host captures the K launches into one CUDA graph.
 #include "kpp_internal.h"
 #include "kpp_pass.cuh"
 
 namespace kpp {
 
 constexpr int kStreamThreads = 256;
-
-// Work after the pass, by the CTA that finishes last: the draw of seed m+1,
-// or phi after the final pass.
-__device__ __forceinline__ void last_cta_epilogue(const Problem &p, int m, double *shd,
-                                                  int64_t *shi)
-{
-    if (m == p.K - 1) { // phi: the ordered FP64 sum of the block sums
-        double total = block_ordered_total<kStreamThreads>(
-            p.nblocks, [&](int64_t k) { return ld_cg(p.block_sums + k); }, shd);
-        if (threadIdx.x == 0 && p.phi)
-            p.phi[0] = total;
-        return;
-    }
-    const int next = m + 1;
-    if (next < p.n_forced) {
-        if (threadIdx.x == 0)
-            p.idx[next] = p.forced[next];
-        return;
-    }
-    const double u = philox_uniform(p.seed, p.stream_id, (uint64_t)next);
-    double T;
-    int64_t pick = hierarchical_draw<kStreamThreads>(p.block_sums, p.nblocks, p.d2, p.N, p.chunk,
-                                                     u, shd, shi, &T);
-    if (threadIdx.x == 0) {
-        if (pick < 0) { // sum D^2 == 0: fewer distinct points than K
-            for (int k = next; k < p.K; ++k)
-                p.idx[k] = -1;
-            if (p.phi)
-                p.phi[0] = T;
-            p.ctl->status = KPP_ERR_DEGENERATE;
-        } else {
-            p.idx[next] = pick;
-        }
-    }
-}
 
 // Returns the centre of pass m, or -1 if the kernel must stop.
 __device__ __forceinline__ int64_t pass_centre(const Problem &p, int m)
@@ -58,7 +22,7 @@ __device__ __forceinline__ int64_t pass_centre(const Problem &p, int m)
     int64_t ci = (m == 0) ? first_seed(p) : __ldcg(p.idx + m);
     if (ci < 0 || ci >= p.N) {
         if (threadIdx.x == 0 && blockIdx.x == 0)
-            p.ctl->status = KPP_ERR_INVALID_ARG;
+            atomicCAS(&p.ctl->status, KPP_OK, KPP_ERR_INVALID_ARG);
         return -1;
     }
     if (m == 0 && blockIdx.x == 0 && threadIdx.x == 0)
@@ -66,27 +30,111 @@ __device__ __forceinline__ int64_t pass_centre(const Problem &p, int m)
     return ci;
 }
 
-// Block sum, ticket, and the last CTA's epilogue.
-__device__ __forceinline__ void finish_pass(const Problem &p, int m, const Acc2 &acc)
+// Block sum, ticket, and -- in the CTA that finishes last -- the draw of
+// seed m+1 (or phi after the final pass): the block holding t = u * T from
+// the block sums, the segment within it, then the point.
+__device__ __forceinline__ void finish_pass(const Problem &p, int m, const Pair &wseg)
 {
-    __shared__ double shd[kStreamThreads / 32 + 1];
-    __shared__ int64_t shi[kStreamThreads / 32];
+    __shared__ float2 segsum[kStreamThreads / 32];
+    __shared__ float2 stage_pairs[kStage];
+    __shared__ float stage_rows[kStage];
+    __shared__ RowsShared rows;
     __shared__ int is_last;
-    __threadfence(); // this thread's D^2 stores before the ticket
-    double s = block_sum<kStreamThreads>(acc.value(), shd);
+    __shared__ int64_t blk_sh, seg_sh;
+    __shared__ Pair before_sh;
+    __shared__ double t_sh, T_sh;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0)
+        segsum[warp] = make_float2(wseg.hi, wseg.lo);
+    __syncthreads();
     if (threadIdx.x == 0) {
-        p.block_sums[blockIdx.x] = s;
-        __threadfence();
-        unsigned prev = atomicAdd(&p.ctl->ticket, 1u);
+        Pair bs{};
+        for (int w = 0; w < kStreamThreads / 32; ++w)
+            bs.add(Pair{segsum[w].x, segsum[w].y});
+        p.block_sums[blockIdx.x] = make_float2(bs.hi, bs.lo);
+        __threadfence(); // this CTA's D^2, segment and block sums before the ticket
+        const unsigned prev = atomicAdd(&p.ctl->ticket, 1u);
         is_last = (prev == (unsigned)p.nblocks - 1u);
     }
     __syncthreads();
     if (!is_last)
         return;
     __threadfence();
-    last_cta_epilogue(p, m, shd, shi);
-    if (threadIdx.x == 0)
+    for (int k = threadIdx.x; k < p.nblocks; k += blockDim.x)
+        stage_pairs[k] = __ldcg(p.block_sums + k);
+    __syncthreads();
+    const bool final_pass = (m == p.K - 1);
+    const int next = m + 1;
+    const bool forced = !final_pass && next < p.n_forced;
+    if (warp == 0) {
+        const double u = (final_pass || forced) ? 0.0
+                                                : philox_uniform(p.seed, p.stream_id, (uint64_t)next);
+        const PFind r = warp_pfind(
+            p.nblocks, [&](int k) { return Pair{stage_pairs[k].x, stage_pairs[k].y}; }, Pair{}, u,
+            true);
+        if (lane == 0) {
+            T_sh = (double)r.total.hi + (double)r.total.lo;
+            t_sh = r.t;
+            blk_sh = r.index;
+            before_sh = r.before;
+            if (r.index < 0) { // rounding left no block above t: the last with weight
+                blk_sh = r.last_positive;
+                before_sh = Pair{};
+                t_sh = INFINITY;
+            }
+        }
+    }
+    __syncthreads();
+    if (final_pass || forced || !(T_sh > 0.0)) {
+        if (threadIdx.x == 0) {
+            if (final_pass) {
+                if (p.phi)
+                    p.phi[0] = T_sh;
+            } else if (forced) {
+                p.idx[next] = p.forced[next];
+            } else { // sum D^2 == 0: fewer distinct points than K
+                for (int k = next; k < p.K; ++k)
+                    p.idx[k] = -1;
+                if (p.phi)
+                    p.phi[0] = T_sh;
+                atomicCAS(&p.ctl->status, KPP_OK, KPP_ERR_DEGENERATE);
+            }
+            p.ctl->ticket = 0u;
+        }
+        return;
+    }
+    const int64_t blk = blk_sh;
+    const int64_t row0 = blk * p.chunk;
+    const int64_t rows_blk = (p.N - row0) < p.chunk ? (p.N - row0) : p.chunk;
+    if (warp == 0) {
+        const float2 *segs = p.seg_sums + blk * (int64_t)p.nseg;
+        const PFind r = warp_pfind(
+            p.nseg,
+            [&](int k) {
+                const float2 v = __ldcg(segs + k);
+                return Pair{v.x, v.y};
+            },
+            before_sh, t_sh, false);
+        if (lane == 0) {
+            if (r.index >= 0) {
+                seg_sh = r.index;
+                before_sh = r.before;
+            } else {
+                seg_sh = r.last_positive >= 0 ? r.last_positive : 0;
+                t_sh = INFINITY;
+            }
+        }
+    }
+    __syncthreads();
+    int64_t first, last;
+    segment_rows(row0, rows_blk, p.sw, p.nseg, (int)seg_sh, &first, &last);
+    const int64_t pick = block_rows_find(
+        first, last, [&](int64_t row) { return __ldcg(p.d2 + row); }, before_sh, t_sh,
+        stage_rows, &rows);
+    if (threadIdx.x == 0) {
+        p.idx[next] = pick;
         p.ctl->ticket = 0u; // ready for the next launch
+    }
 }
 
 template <int DT, int D, int L>
@@ -98,10 +146,16 @@ __global__ void __launch_bounds__(kStreamThreads)
         return;
     CentreRegs<DT, D, L> cr;
     cr.load(p.points, p.scales, ci);
-    const int64_t r0 = (int64_t)blockIdx.x * p.chunk;
-    const int64_t r1 = (r0 + p.chunk) < p.N ? (r0 + p.chunk) : p.N;
-    Acc2 acc = pass_rows<DT, D, L>(p.points, p.scales, p.d2, r0, r1, m == 0, cr);
-    finish_pass(p, m, acc);
+    PassIO io{};
+    io.r0 = (int64_t)blockIdx.x * p.chunk;
+    io.r1 = (io.r0 + p.chunk) < p.N ? (io.r0 + p.chunk) : p.N;
+    io.first = (m == 0);
+    io.gpts = reinterpret_cast<const char *>(p.points);
+    io.scales = p.scales;
+    io.d2 = p.d2;
+    io.segs = p.seg_sums + (int64_t)blockIdx.x * p.nseg;
+    const Pair w = pass_rows<DT, D, L, D2_INPLACE>(io, cr);
+    finish_pass(p, m, w);
 }
 
 template <int DT>
@@ -114,10 +168,16 @@ __global__ void __launch_bounds__(kStreamThreads)
         return;
     load_centre_smem<DT>(p.points, p.scales, ci, p.d, c_sh);
     __syncthreads();
-    const int64_t r0 = (int64_t)blockIdx.x * p.chunk;
-    const int64_t r1 = (r0 + p.chunk) < p.N ? (r0 + p.chunk) : p.N;
-    Acc2 acc = pass_rows_generic<DT>(p.points, p.scales, p.d2, r0, r1, p.d, m == 0, c_sh);
-    finish_pass(p, m, acc);
+    PassIO io{};
+    io.r0 = (int64_t)blockIdx.x * p.chunk;
+    io.r1 = (io.r0 + p.chunk) < p.N ? (io.r0 + p.chunk) : p.N;
+    io.first = (m == 0);
+    io.gpts = reinterpret_cast<const char *>(p.points);
+    io.scales = p.scales;
+    io.d2 = p.d2;
+    io.segs = p.seg_sums + (int64_t)blockIdx.x * p.nseg;
+    const Pair w = pass_rows_generic<DT>(io, p.d, c_sh);
+    finish_pass(p, m, w);
 }
 
 // ---------------------------------------------------------------------------
@@ -138,10 +198,9 @@ constexpr Spec make_spec()
     return Spec{DT, D, Geom<DT, D, L>::L, Geom<DT, D, L>::SW, &streamed_pass_kernel<DT, D, L>};
 }
 
-// Only combinations whose lanes divide the row's vectors are valid; the
-// table below lists, per dtype, the ones that compile for that dtype.
+// Only combinations whose lanes divide the row's 16-byte vectors are valid.
 const Spec kSpecs[] = {
-    // FP32: rows of 8, 16, 32, 64, 128, 256, 512 bytes
+    // FP32: rows of 8 .. 512 bytes
     make_spec<KPP_F32, 2, 1>(), make_spec<KPP_F32, 4, 1>(), make_spec<KPP_F32, 8, 1>(),
     make_spec<KPP_F32, 8, 2>(), make_spec<KPP_F32, 16, 2>(), make_spec<KPP_F32, 16, 4>(),
     make_spec<KPP_F32, 32, 2>(), make_spec<KPP_F32, 32, 4>(), make_spec<KPP_F32, 32, 8>(),
@@ -174,8 +233,8 @@ PassFn generic_fn(int dt)
 
 } // namespace
 
-// Picks the specialisation: requested lanes if built, else the default
-// (8 lanes, or the widest built below that).
+// Picks the specialisation: the requested lanes if built, else the default
+// (8 lanes, or the widest built below that); the generic kernel otherwise.
 bool streamed_lookup(int dt, int d, int lanes, StreamedKernel *out)
 {
     const Spec *best = nullptr;
@@ -204,6 +263,12 @@ bool streamed_lookup(int dt, int d, int lanes, StreamedKernel *out)
 }
 
 int streamed_threads() { return kStreamThreads; }
+int streamed_segments() { return kStreamThreads / 32; }
+
+size_t streamed_smem(const StreamedKernel &k, int d)
+{
+    return k.generic ? 2 * sizeof(float) * (size_t)d : 0;
+}
 
 cudaError_t streamed_launch(const StreamedKernel &k, int grid, const Problem &p, int m,
                             cudaStream_t stream)
@@ -211,8 +276,8 @@ cudaError_t streamed_launch(const StreamedKernel &k, int grid, const Problem &p,
     Problem pp = p;
     int mm = m;
     void *args[] = {&pp, &mm};
-    size_t smem = k.generic ? sizeof(float) * (size_t)p.d : 0;
-    return cudaLaunchKernel(k.fn, dim3(grid), dim3(kStreamThreads), args, smem, stream);
+    return cudaLaunchKernel(k.fn, dim3(grid), dim3(kStreamThreads), args, streamed_smem(k, p.d),
+                            stream);
 }
 
 } // namespace kpp

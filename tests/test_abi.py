@@ -29,7 +29,7 @@ def lib():
 def test_header_declares_the_boundary():
     names = declared_entry_points()
     for required in ["kpp_seed", "kpp_workspace_size", "kpp_read_status", "kpp_quantize",
-                     "kpp_seed_host", "kpp_status_string", "kpp_version"]:
+                     "kpp_seed_host", "kpp_status_string", "kpp_version", "kpp_describe"]:
         assert required in names
 
 
@@ -67,3 +67,30 @@ def test_invalid_arguments_fail_synchronously(lib):
     assert kpp.kpp_workspace_size(10, 0, 1, 0) == 0
     assert kpp.kpp_workspace_size(10, 2, 1, 7) == 0
     assert kpp.kpp_quantize(None, 4, 4, kpp.BF16, None, None, None) == kpp.ERR_INVALID_ARG
+
+
+def test_ctypes_structs_match_the_header(tmp_path):
+    """The binding's kpp_options / kpp_plan mirror the C layout field by field."""
+    import ctypes
+
+    import paper_1908_02136_gb300 as kpp
+
+    src = tmp_path / "layout.c"
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "kpp.h"', "int main(void){"]
+    for cname, py in (("kpp_options", kpp.Options), ("kpp_plan", kpp.Plan)):
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            lines.append(f'printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines.append("return 0;}")
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for cname, py in (("kpp_options", kpp.Options), ("kpp_plan", kpp.Plan)):
+        assert got[(cname, "size")] == ctypes.sizeof(py)
+        for f, _ in py._fields_:
+            assert got[(cname, f)] == getattr(py, f).offset, (cname, f)
+    with pytest.raises(KeyError):
+        kpp._opts_ptr({"no_such_option": 1})

@@ -15,6 +15,8 @@ from paper_1908_02136_gb300 import datagen
 pytestmark = pytest.mark.gpu
 
 DEV = "cuda:0"
+STREAMED, PERSISTENT = kpp.FORM_STREAMED, kpp.FORM_PERSISTENT
+FORMS = [STREAMED, PERSISTENT]
 
 
 def run(points_np, K, seed, stream_id=0, *, dtype="f32", opts=None, forced=None, check=True):
@@ -42,37 +44,56 @@ EXACT_SHAPES = [(5000, 2, 16), (7777, 4, 33), (4097, 8, 40), (20011, 16, 64), (2
                 (3001, 64, 20), (4099, 128, 12), (1000, 3, 10), (999, 5, 9), (2500, 96, 8)]
 
 
+def _form_ok(form, d):
+    # the persistent form is built for d in {2,4,...,128}; others use the streamed form
+    return form == STREAMED or d in (2, 4, 8, 16, 32, 64, 128)
+
+
+@pytest.mark.parametrize("form", FORMS)
 @pytest.mark.parametrize("dtype", ["f32", "bf16"])
 @pytest.mark.parametrize("N,d,K", EXACT_SHAPES)
-def test_exact_regime_bit_identical(N, d, K, dtype):
+def test_exact_regime_bit_identical(N, d, K, dtype, form):
     x = datagen.integer_points(N, d, seed=N + d, n_comp=8)
-    st, sc, idx, d2, phi = run(x, K, seed=17, dtype=dtype)
+    if not _form_ok(form, d):
+        with pytest.raises(kpp.KppError) as e:
+            run(x, K, seed=17, dtype=dtype, opts={"form": form})
+        assert e.value.status == kpp.ERR_UNSUPPORTED
+        return
+    # small blocks so that even these sizes span several CTAs
+    opts = {"form": form, "min_rows_per_cta": 256}
+    st, sc, idx, d2, phi = run(x, K, seed=17, dtype=dtype, opts=opts)
     parity.check(st, K, 17, 0, idx, d2, phi, scales=sc, exact=True)
 
 
 @pytest.mark.parametrize("N,d,K,ncomp", [(10_000, 2, 16, 16), (100_003, 32, 64, 64),
                                          (50_001, 64, 48, 32), (30_011, 128, 32, 32),
                                          (12_345, 8, 100, 50), (9_999, 7, 20, 10)])
-def test_float_regime_f32(N, d, K, ncomp):
+@pytest.mark.parametrize("form", FORMS)
+def test_float_regime_f32(N, d, K, ncomp, form):
     x = datagen.gmm(N, d, ncomp, seed=N, mean_box=50.0)
-    st, sc, idx, d2, phi = run(x, K, seed=1)
+    if not _form_ok(form, d):
+        return
+    st, sc, idx, d2, phi = run(x, K, seed=1, opts={"form": form, "min_rows_per_cta": 512})
     events = parity.check(st, K, 1, 0, idx, d2, phi)
     assert events <= 1
 
 
-def test_paper_scale_small_workload():
+@pytest.mark.parametrize("form", FORMS)
+def test_paper_scale_small_workload(form):
     wl = datagen.WORKLOADS["gmm-N1e4-d2-K16"]
     x = datagen.workload_points(wl)
-    st, sc, idx, d2, phi = run(x, wl.K, seed=wl.draw_seed)
+    st, sc, idx, d2, phi = run(x, wl.K, seed=wl.draw_seed, opts={"form": form})
     assert parity.check(st, wl.K, wl.draw_seed, 0, idx, d2, phi) == 0
 
 
 @pytest.mark.parametrize("dtype", ["bf16", "fp8"])
 @pytest.mark.parametrize("N,d,K", [(40_003, 16, 32), (20_001, 64, 24), (10_007, 128, 16),
                                    (8_191, 2, 12), (6_001, 4, 12), (5_003, 8, 10)])
-def test_float_regime_low_precision_storage(N, d, K, dtype):
+@pytest.mark.parametrize("form", FORMS)
+def test_float_regime_low_precision_storage(N, d, K, dtype, form):
     x = datagen.gmm(N, d, K, seed=N + 1, mean_box=50.0)
-    st, sc, idx, d2, phi = run(x, K, seed=5, dtype=dtype)
+    st, sc, idx, d2, phi = run(x, K, seed=5, dtype=dtype,
+                               opts={"form": form, "min_rows_per_cta": 1024})
     events = parity.check(st, K, 5, 0, idx, d2, phi, scales=sc)
     assert events <= 1
 
@@ -82,83 +103,131 @@ def test_float_regime_low_precision_storage(N, d, K, dtype):
                                      (128, 32)])
 def test_every_lanes_per_row_variant(d, lanes):
     x = datagen.integer_points(9001, d, seed=d * lanes, n_comp=6)
-    opts = {"lanes_per_row": lanes}
+    opts = {"lanes_per_row": lanes, "form": STREAMED}
     st, sc, idx, d2, phi = run(x, 24, seed=3, opts=opts)
     parity.check(st, 24, 3, 0, idx, d2, phi, exact=True)
 
 
 def test_unbuilt_lanes_variant_is_rejected():
     x = torch.zeros((100, 32), device=DEV)
-    with pytest.raises(kpp.KppError) as e:
-        kpp.seed(x, 4, 1, opts={"lanes_per_row": 32})
-    assert e.value.status == kpp.ERR_UNSUPPORTED
+    for form in FORMS:
+        with pytest.raises(kpp.KppError) as e:
+            kpp.seed(x, 4, 1, opts={"lanes_per_row": 32, "form": form})
+        assert e.value.status == kpp.ERR_UNSUPPORTED
 
 
 def test_graph_and_plain_launches_agree_and_repeat():
     x = datagen.gmm(60_000, 32, 32, seed=2)
-    a = run(x, 40, seed=9)
-    b = run(x, 40, seed=9, opts={"use_graph": -1})
-    c = run(x, 40, seed=9)  # graph cache hit
+    a = run(x, 40, seed=9, opts={"form": STREAMED})
+    b = run(x, 40, seed=9, opts={"use_graph": -1, "form": STREAMED})
+    c = run(x, 40, seed=9, opts={"form": STREAMED})  # graph cache hit
     for other in (b, c):
         assert np.array_equal(a[2], other[2])
         assert np.array_equal(a[3], other[3])
         assert a[4] == other[4]
 
 
-def test_ctas_per_sm_changes_blocking_not_results_in_exact_regime():
+def test_blocking_changes_nothing_in_exact_regime():
     x = datagen.integer_points(50_000, 16, seed=4, n_comp=8)
-    ref = run(x, 30, seed=4)
-    for per_sm in (1, 2, 3):
-        o = run(x, 30, seed=4, opts={"ctas_per_sm": per_sm})
-        assert np.array_equal(ref[2], o[2]) and np.array_equal(ref[3], o[3])
+    ref = run(x, 30, seed=4, opts={"form": STREAMED})
+    variants = [{"form": STREAMED, "ctas_per_sm": c} for c in (1, 2, 3)]
+    variants += [{"form": PERSISTENT, "min_rows_per_cta": r} for r in (256, 1000, 5000, 60_000)]
+    variants += [{"form": PERSISTENT, "ctas_per_sm": 2, "min_rows_per_cta": 128}]
+    for o in variants:
+        v = run(x, 30, seed=4, opts=o)
+        assert np.array_equal(ref[2], v[2]) and np.array_equal(ref[3], v[3]), o
+        assert ref[4] == v[4], o
 
 
-def test_k1_and_k_equals_n():
+@pytest.mark.parametrize("opts", [
+    {"smem_cache": -1}, {"smem_cache": 0}, {"smem_cache": 1024}, {"alternate": -1},
+    {"alternate": 1}, {"l2_policy": -1}, {"l2_policy": 2}, {"l2_policy": 0},
+    # D^2 too large for shared memory: kept in the output array
+    {"min_rows_per_cta": 70_000, "smem_cache": -1},
+    {"min_rows_per_cta": 70_000, "smem_cache": 0},
+])
+def test_persistent_options_exact(opts):
+    x = datagen.integer_points(150_001, 8, seed=12, n_comp=16)
+    o = dict(opts, form=PERSISTENT)
+    o.setdefault("min_rows_per_cta", 2048)
+    st, sc, idx, d2, phi = run(x, 40, seed=21, opts=o)
+    parity.check(st, 40, 21, 0, idx, d2, phi, exact=True)
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16", "fp8"])
+def test_persistent_d2_in_global_float(dtype):
+    x = datagen.gmm(200_003, 32, 64, seed=13)
+    o = {"form": PERSISTENT, "min_rows_per_cta": 70_000}
+    st, sc, idx, d2, phi = run(x, 48, seed=2, dtype=dtype, opts=o)
+    assert parity.check(st, 48, 2, 0, idx, d2, phi, scales=sc) <= 1
+
+
+def test_barrier_timeout_is_reported_not_hung():
+    # A 1 us bound on every grid-barrier wait cannot hold across 64 passes over
+    # 10^6 points: some CTA gives up, records the timeout and every CTA exits.
+    x = torch.from_numpy(datagen.gmm(1_000_000, 32, 32, seed=3)).to(DEV)
+    with pytest.raises(kpp.KppError) as e:
+        kpp.seed(x, 64, 1, opts={"form": PERSISTENT, "timeout_us": 1})
+    assert e.value.status == kpp.ERR_TIMEOUT
+    # the context is still usable and a normal call succeeds afterwards
+    idx, d2, phi = kpp.seed(x, 64, 1, opts={"form": PERSISTENT})
+    assert int((idx >= 0).sum()) == 64
+
+
+@pytest.mark.parametrize("form", FORMS)
+def test_k1_and_k_equals_n(form):
     x = datagen.gmm(257, 4, 4, seed=8)
-    st, sc, idx, d2, phi = run(x, 1, seed=2)
+    st, sc, idx, d2, phi = run(x, 1, seed=2, opts={"form": form})
     parity.check(st, 1, 2, 0, idx, d2, phi)
-    st, sc, idx, d2, phi = run(x, 257, seed=2)
+    st, sc, idx, d2, phi = run(x, 257, seed=2, opts={"form": form})
     assert sorted(idx.tolist()) == list(range(257))
     assert np.all(d2 == 0) and phi == 0.0
 
 
-def test_single_point():
+@pytest.mark.parametrize("form", FORMS)
+def test_single_point(form):
     x = np.array([[1.5, -2.0]], np.float32)
-    st, sc, idx, d2, phi = run(x, 1, seed=0)
+    st, sc, idx, d2, phi = run(x, 1, seed=0, opts={"form": form})
     assert idx.tolist() == [0] and d2.tolist() == [0.0] and phi == 0.0
 
 
-def test_degenerate_data_reports_status():
+@pytest.mark.parametrize("form", FORMS)
+def test_degenerate_data_reports_status(form):
     base = np.array([[0, 0, 0, 0], [1, 2, 3, 4], [5, 5, 5, 5]], np.float32)
     x = np.repeat(base, [400, 300, 301], axis=0)
     rng = np.random.default_rng(0)
     x = x[rng.permutation(len(x))]
+    o = {"form": form, "min_rows_per_cta": 128}
     with pytest.raises(kpp.KppError) as e:
-        run(x, 5, seed=1)
+        run(x, 5, seed=1, opts=o)
     assert e.value.status == kpp.ERR_DEGENERATE
-    st, sc, idx, d2, phi = run(x, 5, seed=1, check=False)
+    st, sc, idx, d2, phi = run(x, 5, seed=1, check=False, opts=o)
     assert np.all(idx[3:] == -1) and phi == 0.0
     parity.check(st, 5, 1, 0, idx, d2, phi, exact=True, status=oracle.DEGENERATE)
 
 
-def test_forced_prefix_replays_the_oracle():
+@pytest.mark.parametrize("form", FORMS)
+def test_forced_prefix_replays_the_oracle(form):
     x = datagen.gmm(30_000, 16, 16, seed=6)
     r = oracle.seed(x, 20, 4)
-    st, sc, idx, d2, phi = run(x, 20, seed=4, forced=r["idx"])
+    o = {"form": form, "min_rows_per_cta": 1024}
+    st, sc, idx, d2, phi = run(x, 20, seed=4, forced=r["idx"], opts=o)
     assert np.array_equal(idx, r["idx"])
     np.testing.assert_allclose(d2, r["d2"], rtol=1e-5)
     # a partial prefix: the GPU continues with its own draws after it
-    st, sc, idx2, d2, phi = run(x, 20, seed=4, forced=r["idx"][:7])
+    st, sc, idx2, d2, phi = run(x, 20, seed=4, forced=r["idx"][:7], opts=o)
     assert np.array_equal(idx2[:7], r["idx"][:7])
     parity.check(st, 20, 4, 0, idx2, d2, phi)
 
 
-def test_bad_forced_index_is_a_device_error():
+@pytest.mark.parametrize("form", FORMS)
+def test_bad_forced_index_is_a_device_error(form):
     x = torch.zeros((64, 4), device=DEV)
     x[:, 0] = torch.arange(64, device=DEV, dtype=torch.float32)
-    with pytest.raises(kpp.KppError) as e:
-        kpp.seed(x, 3, 1, forced=[5, 64])
-    assert e.value.status == kpp.ERR_INVALID_ARG
+    for forced in ([5, 64], [-1], [3, 7, 1 << 40]):
+        with pytest.raises(kpp.KppError) as e:
+            kpp.seed(x, 3, 1, forced=forced, opts={"form": form})
+        assert e.value.status == kpp.ERR_INVALID_ARG
 
 
 def test_streams_give_independent_draws():
@@ -197,10 +266,12 @@ def test_seed_host_matches_device_seed():
 
 
 @pytest.mark.slow
-def test_full_size_workload_parity():
-    """The bench workload (10^6 x 32, K=256) in the bench's launch configuration."""
+@pytest.mark.parametrize("form", FORMS)
+def test_full_size_workload_parity(form):
+    """The bench workload (10^6 x 32, K=256) in the bench's launch configuration
+    (the persistent form with default options is what bench.py times)."""
     wl = datagen.WORKLOADS["gmm-N1e6-d32-K256"]
     x = datagen.workload_points(wl)
-    st, sc, idx, d2, phi = run(x, wl.K, seed=wl.draw_seed)
+    st, sc, idx, d2, phi = run(x, wl.K, seed=wl.draw_seed, opts={"form": form})
     events = parity.check(st, wl.K, wl.draw_seed, 0, idx, d2, phi)
     assert events <= 2
