@@ -205,6 +205,42 @@ KPP_API kpp_status kpp_read_status(const void *workspace, kpp_stream_t stream);
 KPP_API kpp_status kpp_quantize(const float *x, int64_t N, int32_t d, kpp_dtype to, void *out,
                         float *row_scales, kpp_stream_t stream);
 
+/*
+ * Seeding for callers that cannot allocate device memory.  (The paper has
+ * no counterpart; this is a calling convention of this library.)
+ *
+ * kpp_seed needs a caller-provided workspace.  Some callers cannot provide
+ * one: code running under an allocator or memory pool it does not own and
+ * may not grow, plugin code that is handed only its inputs and outputs, and
+ * latency-critical paths where cudaMalloc -- which can synchronise the whole
+ * device -- is not allowed.  kpp_seed_noalloc runs the persistent form with
+ * its scratch in a fixed 16 KiB array inside the library (a static device
+ * variable that every GPU loading the library holds until process exit),
+ * and calls no cudaMalloc, cudaFree or allocating routine.
+ *
+ *   Arguments as kpp_seed, without forced prefix and workspace; `opts` may
+ *   tune the persistent form (its `form` field is ignored).
+ *   device_status  optional HOST pointer: if given, the call synchronises
+ *                  `stream` and stores the device status there (KPP_OK,
+ *                  KPP_ERR_DEGENERATE, KPP_ERR_TIMEOUT); if NULL the call
+ *                  stays asynchronous.
+ * Returns KPP_ERR_WORKSPACE if the problem's plan needs more scratch than
+ * the fixed array holds (more than 252 CTAs), KPP_ERR_UNSUPPORTED if the
+ * persistent form is not built for (dtype, d), or kpp_seed's other errors.
+ *
+ * The first call on each device looks up the array's device address while
+ * that device is current; make that first call before any stream capture.
+ * All calls share the one array and it keeps the last call's contents (each
+ * call clears what must start at zero), so calls whose work overlaps on the
+ * GPU -- on different streams, or from different threads -- race; serialise
+ * them on one stream.
+ */
+KPP_API kpp_status kpp_seed_noalloc(const void *points, const float *row_scales, int64_t N,
+                                    int32_t d, int32_t K, kpp_dtype dtype, uint64_t seed,
+                                    uint64_t stream_id, int64_t *indices_out, float *d2_out,
+                                    double *phi_out, kpp_stream_t stream,
+                                    const kpp_options *opts, int32_t *device_status);
+
 #ifdef __cplusplus
 }
 #endif

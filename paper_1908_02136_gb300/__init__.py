@@ -96,6 +96,9 @@ def load_library(build_if_stale: bool = True):
         lib.kpp_seed_host.argtypes = [P, P, P, P, I64, I32, I32, ctypes.c_int, U64, U64, P, P, P,
                                       P, P, P, P, ctypes.c_size_t, P, P]
         lib.kpp_seed_host.restype = ctypes.c_int
+        lib.kpp_seed_noalloc.argtypes = [P, P, I64, I32, I32, ctypes.c_int, U64, U64, P, P, P,
+                                         P, P, P]
+        lib.kpp_seed_noalloc.restype = ctypes.c_int
         lib.kpp_read_status.argtypes = [P, P]
         lib.kpp_read_status.restype = ctypes.c_int
         lib.kpp_quantize.argtypes = [P, I64, I32, ctypes.c_int, P, P, P]
@@ -154,6 +157,17 @@ def kpp_seed_host(host_points, host_scales, dev_points, dev_scales, N, d, K, dty
                                         K, dtype, seed, stream_id, host_indices, host_d2,
                                         host_phi, dev_indices, dev_d2, dev_phi, workspace,
                                         workspace_bytes, stream, _opts_ptr(opts))
+
+
+def kpp_seed_noalloc(points, row_scales, N, d, K, dtype, seed, stream_id, indices_out, d2_out,
+                     phi_out, stream, opts=None, device_status=None) -> int:
+    """Seeding with the library's fixed internal scratch (no workspace, no
+    allocation); ``device_status`` is a ctypes int32 (or None) that receives
+    the device status after a stream synchronisation."""
+    ds = None if device_status is None else ctypes.byref(device_status)
+    return load_library().kpp_seed_noalloc(points, row_scales, N, d, K, dtype, seed, stream_id,
+                                           indices_out, d2_out, phi_out, stream,
+                                           _opts_ptr(opts), ds)
 
 
 def kpp_read_status(workspace, stream) -> int:
