@@ -138,17 +138,19 @@ kpp_status plan_persistent_at(int64_t N, int32_t K, const kpp_options &o, int sm
         chunk = min_rows;
     chunk = (chunk + a - 1) / a * a;
     const int nblocks = (int)((N + chunk - 1) / chunk);
-    if ((uint64_t)K * (uint64_t)nblocks >= (1ull << 32))
-        return KPP_ERR_UNSUPPORTED; // barrier counter range
+    if (nblocks > persistent_max_blocks())
+        return KPP_ERR_UNSUPPORTED;
     // shared memory: D^2 of the block if it fits, then as many cached rows as fit
     cudaFuncAttributes fa;
     if (cudaFuncGetAttributes(&fa, pl->pk.fn_smem) != cudaSuccess)
         return KPP_ERR_CUDA;
     const int64_t budget = ((int64_t)optin - (int64_t)fa.sharedSizeBytes - 1024) / per_sm;
     int64_t used = 0;
-    bool d2_in_smem = (int64_t)sizeof(float) * chunk <= budget;
+    // D^2 of the block and its 32-row chunk sums
+    const int64_t d2_bytes = ((4 * chunk + 15) & ~15ll) + 8 * ((chunk + 31) / 32);
+    bool d2_in_smem = d2_bytes <= budget;
     if (d2_in_smem)
-        used += (int64_t)sizeof(float) * chunk;
+        used += d2_bytes;
     // the cache holds the first `supers` super-iterations of every warp's
     // segment (so that all warps read the same share from shared memory)
     const int nseg = persistent_segments();
@@ -165,7 +167,7 @@ kpp_status plan_persistent_at(int64_t N, int32_t K, const kpp_options &o, int sm
             supers = 0;
     }
     pl->pfn = d2_in_smem ? pl->pk.fn_smem : pl->pk.fn_global;
-    pl->psmem = (size_t)(supers * unit + (d2_in_smem ? 4 * chunk : 0));
+    pl->psmem = (size_t)(supers * unit + (d2_in_smem ? d2_bytes : 0));
     // static + dynamic shared memory above 48 KB needs the opt-in attribute
     if (cudaFuncSetAttribute(pl->pfn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)pl->psmem) != cudaSuccess)

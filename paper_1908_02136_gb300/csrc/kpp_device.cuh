@@ -275,24 +275,96 @@ __device__ __forceinline__ Pair warp_pair_scan(Pair v, Pair &excl)
 }
 
 // ---------------------------------------------------------------------------
-// Warp-level inverse-CDF search (the draw), FP32 two-sum pairs throughout
-// and FP64 only where a decision is taken: t = u * T and the comparisons
-// "prefix > t", which are exact (a pair converts to FP64 exactly whenever its
-// parts are integers, as they are for integer coordinates).
-//
-// Over n values v_k >= 0 (get(k) returns a Pair): lane l sums the contiguous
-// slice [l*per, (l+1)*per) in order; the slice sums are prefix-summed over
-// lanes; the first lane whose running total exceeds t is walked element by
-// element, one element per lane.  The result is the first k with v_k > 0 and
-// base + prefix_k > t, where t = u * (base + total) in `u_mode`, else t =
-// u_or_t.  Every lane returns the same result.  n <= 1024.
+// The draw's threshold t = u * T.  Decisions "prefix > t" are taken on an
+// FP32 pair approximation of t (relative error below 2^-44) whenever the
+// prefix is farther than tol = 2^-40 * t from it -- then the answer is
+// certain -- and otherwise (a near tie, rare) in FP64 against the exact
+// t = fl64(u * T), the value the FP64 oracle uses.  FP64 is slow on this GPU
+// (a dependent add costs ~64 cycles against ~5 for FP32), so the common case
+// avoids it entirely.
+// ---------------------------------------------------------------------------
+// Exact FP64 decision of a near tie: (P.hi + P.lo) > u * (T.hi + T.lo).
+// Out of line so that the compiler branches around it instead of computing
+// it (predicated) on every comparison.
+static __device__ __noinline__ bool pair_gt_exact(float phi, float plo, double u, float Thi, float Tlo)
+{
+    return (double)phi + (double)plo > u * ((double)Thi + (double)Tlo);
+}
+
+struct Thresh {
+    float hi, lo; // approximation of t
+    float tol;
+    float uh, ul; // u split into two floats
+    double u;
+    Pair T;
+    int inf; // t = +infinity: no prefix exceeds it
+
+    __device__ __forceinline__ double exact() const
+    {
+        return u * ((double)T.hi + (double)T.lo);
+    }
+    // prefix P > t ?
+    __device__ __forceinline__ bool gt(const Pair &P) const
+    {
+        if (inf)
+            return false;
+        const float d = __fadd_rn(__fsub_rn(P.hi, hi), __fsub_rn(P.lo, lo));
+        if (d > tol)
+            return true;
+        if (d < -tol)
+            return false;
+        return pair_gt_exact(P.hi, P.lo, u, T.hi, T.lo);
+    }
+};
+
+// u and its float split; the FP64 work here is off the draw's critical path.
+__device__ __forceinline__ Thresh thresh_for_u(double u)
+{
+    Thresh th;
+    th.u = u;
+    th.uh = (float)u;
+    th.ul = (float)(u - (double)th.uh);
+    th.hi = th.lo = th.tol = 0.f;
+    th.T = Pair{0.f, 0.f};
+    th.inf = 0;
+    return th;
+}
+
+// Completes a threshold once T is known: t ~ uh*T.hi + (exact error of that
+// product) + uh*T.lo + ul*T.hi, all in FP32.
+__device__ __forceinline__ void thresh_set_total(Thresh &th, const Pair &T)
+{
+    th.T = T;
+    const float p = __fmul_rn(th.uh, T.hi);
+    const float e = __fmaf_rn(th.uh, T.hi, -p);
+    th.hi = p;
+    th.lo = __fadd_rn(e, __fmaf_rn(th.uh, T.lo, __fmul_rn(th.ul, T.hi)));
+    th.tol = fabsf(p) * 0x1.0p-40f + 0x1.0p-126f;
+}
+
+__device__ __forceinline__ Thresh thresh_inf()
+{
+    Thresh th = thresh_for_u(0.0);
+    th.inf = 1;
+    return th;
+}
+
+// ---------------------------------------------------------------------------
+// Warp-level inverse-CDF search (the draw) over n values v_k >= 0 (get(k)
+// returns a Pair), in FP32 two-sum pairs.  Lane l sums the contiguous slice
+// [l*per, (l+1)*per) in order; slice sums are prefix-summed over lanes; the
+// first lane whose running total exceeds t is walked element by element, one
+// element per lane.  The result is the first k with v_k > 0 and
+// base + prefix_k > t.  With `u_mode`, the threshold's total is first set to
+// base + (sum of all values).  Every lane returns the same result.
+// n <= 1024.
 // ---------------------------------------------------------------------------
 struct PFind {
     int64_t index;         // first crossing, or -1
     int64_t last_positive; // largest k with v_k > 0, or -1
     Pair before;           // base + prefix before the crossing
     Pair total;            // base + sum of all values
-    double t;              // the threshold used
+    Thresh th;             // the threshold used
 };
 
 __device__ __forceinline__ bool pair_gt(const Pair &p, double t)
@@ -301,54 +373,73 @@ __device__ __forceinline__ bool pair_gt(const Pair &p, double t)
 }
 
 template <class Get>
-__device__ __forceinline__ PFind warp_pfind(int n, Get get, Pair base, double u_or_t, bool u_mode)
+__device__ __forceinline__ PFind warp_pfind(int n, Get get, Pair base, const Thresh &th_in,
+                                            bool u_mode)
 {
     const int lane = threadIdx.x & 31;
     const int per = (n + 31) >> 5;
     const int b = lane * per;
     const int e = b + per < n ? b + per : n;
     Pair own{};
-    int lastpos = -1;
-    for (int k = b; k < e; ++k) {
-        const Pair v = get(k);
-        own.add(v);
-        if (v.hi > 0.f)
-            lastpos = k;
-    }
+    for (int k = b; k < e; ++k)
+        own.add(get(k));
     Pair excl;
     const Pair incl = warp_pair_scan(own, excl);
     PFind r;
     r.before = Pair{};
     r.total = pair_sum(base, shfl_pair(incl, 31));
-    r.t = u_mode ? u_or_t * ((double)r.total.hi + (double)r.total.lo) : u_or_t;
-    const unsigned cross = __ballot_sync(0xffffffffu, b < e && pair_gt(pair_sum(base, incl), r.t));
+    r.th = th_in;
+    if (u_mode)
+        thresh_set_total(r.th, r.total);
+    const Pair start = pair_sum(base, excl);
+    const unsigned cross = __ballot_sync(0xffffffffu, b < e && r.th.gt(pair_sum(base, incl)));
     r.index = -1;
+    r.last_positive = -1;
     if (cross) {
+        // the first lane whose running total passes t walks its own slice;
+        // rounding can leave that walk short of t: then the slice's last point
+        // with weight
         const int L = __ffs(cross) - 1;
-        const Pair start = pair_sum(base, shfl_pair(excl, L));
-        const int k = L * per + lane;
-        const bool in = lane < per && k < n;
-        const Pair v = in ? get(k) : Pair{};
-        Pair vex;
-        const Pair vin = warp_pair_scan(v, vex);
-        const bool hit = in && v.hi > 0.f && pair_gt(pair_sum(start, vin), r.t);
-        const unsigned h = __ballot_sync(0xffffffffu, hit);
-        // rounding can leave the slice's own walk short of t: then its last
-        // point with weight
-        const unsigned pos = __ballot_sync(0xffffffffu, in && v.hi > 0.f);
-        const int j = h ? __ffs(h) - 1 : (pos ? 31 - __clz(pos) : -1);
-        if (j >= 0) {
-            r.index = L * per + j;
-            r.before = pair_sum(start, shfl_pair(vex, j));
+        int idx = -1;
+        Pair before{};
+        if (lane == L) {
+            Pair run = start;
+            int lastpos = -1;
+            Pair lastpos_before{};
+            for (int k = b; k < e; ++k) {
+                const Pair v = get(k);
+                const Pair next = pair_sum(run, v);
+                if (v.hi > 0.f) {
+                    if (r.th.gt(next)) {
+                        idx = k;
+                        before = run;
+                        break;
+                    }
+                    lastpos = k;
+                    lastpos_before = run;
+                }
+                run = next;
+            }
+            if (idx < 0) {
+                idx = lastpos;
+                before = lastpos_before;
+            }
         }
+        r.index = __shfl_sync(0xffffffffu, idx, L);
+        r.before = shfl_pair(before, L);
     }
-    int lp = lastpos;
+    if (r.index < 0) { // no crossing: the last value with weight (rare)
+        int lp = -1;
+        for (int k = b; k < e; ++k)
+            if (get(k).hi > 0.f)
+                lp = k;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const int y = __shfl_xor_sync(0xffffffffu, lp, o);
-        lp = y > lp ? y : lp;
+        for (int o = 16; o > 0; o >>= 1) {
+            const int y = __shfl_xor_sync(0xffffffffu, lp, o);
+            lp = y > lp ? y : lp;
+        }
+        r.last_positive = lp;
     }
-    r.last_positive = lp;
     return r;
 }
 
@@ -368,57 +459,87 @@ __host__ __device__ __forceinline__ void segment_rows(int64_t row0, int64_t rows
 
 constexpr int kStage = 1024; // values staged in shared memory per round
 
-// Shared state of block_rows_find.
-struct RowsShared {
-    int64_t found;
-    int64_t last_positive;
-    Pair total;
+// One-value-per-lane search (n <= 32): the first lane k < n with v_k > 0 and
+// base + prefix_k > t, and the prefix before it; if none, the last lane with
+// weight (index -1 if none at all).  Every lane returns the same result.
+struct Find32 {
+    int index;
+    Pair before;
 };
 
-// Point-level search of a draw over rows [first, last) whose D^2 are read by
-// `get_d2(row)`, in rounds of kStage rows staged in shared memory by the whole
-// block and scanned by warp 0, from prefix `base` against threshold t (+inf:
-// take the last row with weight).  All threads must call it; all return the
-// row (`first` if no row has weight).  `*before` gets the prefix before it.
-template <class GetD2>
-__device__ int64_t block_rows_find(int64_t first, int64_t last, GetD2 get_d2, Pair base, double t,
-                                   float *stage, RowsShared *sh, Pair *before = nullptr)
+__device__ __forceinline__ Find32 warp_find32(int n, Pair v, Pair base, const Thresh &th)
 {
-    int64_t lastpos = -1;
-    Pair lastpos_before{};
-    for (int64_t w0 = first; w0 < last; w0 += kStage) {
-        const int cnt = (int)((last - w0) < kStage ? (last - w0) : kStage);
-        __syncthreads();
-        for (int k = threadIdx.x; k < cnt; k += blockDim.x)
-            stage[k] = get_d2(w0 + k);
-        __syncthreads();
-        if (threadIdx.x < 32) {
-            const PFind r = warp_pfind(
-                cnt, [&](int k) { return Pair{stage[k], 0.f}; }, base, t, false);
-            if (threadIdx.x == 0) {
-                sh->found = r.index >= 0 ? w0 + r.index : -1;
-                sh->last_positive = r.last_positive >= 0 ? w0 + r.last_positive : -1;
-                sh->total = r.index >= 0 ? r.before : r.total;
-            }
-        }
-        __syncthreads();
-        const int64_t f = sh->found, lp = sh->last_positive;
-        const Pair tot = sh->total;
-        if (f >= 0) {
-            if (before)
-                *before = tot;
-            __syncthreads();
-            return f;
-        }
-        if (lp >= 0) {
-            lastpos = lp;
-            lastpos_before = base; // prefix at the start of that round
-        }
-        base = tot;
+    const int lane = threadIdx.x & 31;
+    if (lane >= n)
+        v = Pair{0.f, 0.f};
+    Pair ex;
+    const Pair in = warp_pair_scan(v, ex);
+    const bool pos = lane < n && v.hi > 0.f;
+    const unsigned hit = __ballot_sync(0xffffffffu, pos && th.gt(pair_sum(base, in)));
+    Find32 r;
+    if (hit) {
+        r.index = __ffs(hit) - 1;
+    } else {
+        const unsigned any = __ballot_sync(0xffffffffu, pos);
+        r.index = any ? 31 - __clz(any) : -1;
     }
-    __syncthreads();
-    if (before)
-        *before = lastpos_before;
+    r.before = pair_sum(base, shfl_pair(ex, r.index < 0 ? 0 : r.index));
+    return r;
+}
+
+// Point-level search of a draw by one warp over rows [first, last) whose D^2
+// are read by `get_d2(row)`: lane l sums, in order, the rows of its slice of
+// whole 32-row chunks; the slice sums are prefix-summed over lanes; then the
+// chunks of the first slice whose running total passes t are scanned one at
+// a time with one row per lane.  Returns the first row with D^2 > 0 whose
+// prefix (from `base`) exceeds t -- or, when rounding leaves none, the last
+// row with weight in the crossing slice (the last in the range if t.inf) --
+// and `first` if no row has weight.  All lanes return the same row.
+template <class GetD2>
+__device__ int64_t warp_rows_find(int64_t first, int64_t last, GetD2 get_d2, Pair base,
+                                  const Thresh &th)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t n = last - first;
+    const int64_t nch = (n + 31) / 32;
+    const int64_t pc = (nch + 31) / 32; // chunks per lane
+    const int64_t sb = first + (int64_t)lane * pc * 32;
+    const int64_t se_ = sb + pc * 32;
+    const int64_t se = se_ < last ? se_ : last;
+    Pair own{};
+#pragma unroll 8
+    for (int64_t r = sb; r < se; ++r)
+        own.add(get_d2(r));
+    Pair excl;
+    const Pair incl = warp_pair_scan(own, excl);
+    unsigned cross = __ballot_sync(0xffffffffu, sb < se && th.gt(pair_sum(base, incl)));
+    int L;
+    if (cross) {
+        L = __ffs(cross) - 1;
+    } else { // no slice passes t: the last slice with weight
+        const unsigned pos = __ballot_sync(0xffffffffu, sb < se && own.hi > 0.f);
+        if (!pos)
+            return first;
+        L = 31 - __clz(pos);
+    }
+    Pair run = pair_sum(base, shfl_pair(excl, L));
+    const int64_t lb = first + (int64_t)L * pc * 32;
+    const int64_t le_ = lb + pc * 32;
+    const int64_t le = le_ < last ? le_ : last;
+    int64_t lastpos = -1;
+    for (int64_t c = lb; c < le; c += 32) {
+        const int64_t row = c + lane;
+        const float v = row < le ? get_d2(row) : 0.f;
+        Pair vex;
+        const Pair vin = warp_pair_scan(Pair{v, 0.f}, vex);
+        const unsigned hit = __ballot_sync(0xffffffffu, v > 0.f && th.gt(pair_sum(run, vin)));
+        if (hit)
+            return c + (__ffs(hit) - 1);
+        const unsigned pos = __ballot_sync(0xffffffffu, v > 0.f);
+        if (pos)
+            lastpos = c + (31 - __clz(pos));
+        run = pair_sum(run, shfl_pair(vin, 31));
+    }
     return lastpos >= 0 ? lastpos : first;
 }
 
@@ -499,6 +620,46 @@ __device__ __forceinline__ bool wait_slot(const unsigned long long *a, int m, Co
         if (give_up(ctl, t0, timeout_ns, it, (uint32_t)m))
             return false;
     }
+}
+
+// One warp waits for slots [0, n) of pass m (n <= 32 * 8 per call), storing
+// the unpacked pairs in `out`.  Each lane owns slots lane, lane + 32, ...; all
+// its pending loads are issued before any is checked, so a round costs one
+// memory round trip however many slots a lane owns.  Returns false (on all
+// lanes) if a wait gave up.
+__device__ __forceinline__ bool warp_wait_slots(const unsigned long long *slots, int n, int m,
+                                                Control *ctl, uint64_t timeout_ns, float2 *out)
+{
+    constexpr int kPer = 8;
+    const int lane = threadIdx.x & 31;
+    const uint32_t tag = slot_tag(m);
+    unsigned pending = 0;
+#pragma unroll
+    for (int j = 0; j < kPer; ++j)
+        if (lane + 32 * j < n)
+            pending |= 1u << j;
+    const uint64_t t0 = global_ns();
+    bool ok = true;
+    for (uint32_t it = 1; pending; ++it) {
+        unsigned long long w[kPer];
+#pragma unroll
+        for (int j = 0; j < kPer; ++j)
+            w[j] = (pending >> j) & 1u ? ld_relaxed_u64(slots + (size_t)(lane + 32 * j) * kSlotWords)
+                                       : 0ull;
+#pragma unroll
+        for (int j = 0; j < kPer; ++j) {
+            if (((pending >> j) & 1u) && ((uint32_t)w[j] >> 31) == tag) {
+                const Pair v = unpack_slot(w[j]);
+                out[lane + 32 * j] = make_float2(v.hi, v.lo);
+                pending &= ~(1u << j);
+            }
+        }
+        if (pending && give_up(ctl, t0, timeout_ns, it, (uint32_t)m)) {
+            ok = false;
+            break;
+        }
+    }
+    return __all_sync(0xffffffffu, ok);
 }
 
 // Waits until the mailbox carries pass m's index; returns it, or -1.

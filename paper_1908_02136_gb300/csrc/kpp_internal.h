@@ -41,6 +41,7 @@ struct PersistentKernel {
 
 bool persistent_lookup(int dt, int d, int lanes, PersistentKernel *out);
 int persistent_threads();
+int persistent_max_blocks();
 int persistent_segments();
 cudaError_t persistent_launch(const void *fn, int grid, size_t smem, const Problem &p,
                               const PersistArgs &a, cudaStream_t stream);

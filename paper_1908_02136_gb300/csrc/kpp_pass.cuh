@@ -32,8 +32,10 @@ struct Geom {
     static constexpr int RPV = WIDE ? 1 : 16 / RB;
     static constexpr int SW = WIDE ? 32 : 32 * RPV; // rows per warp super-iteration
     static constexpr int CREG = WIDE ? VPL * EPV : EPV;
-    // slots per unrolled batch, so at most 8 vectors per lane are in flight
-    static constexpr int JB = WIDE ? ((8 / VPL) < 1 ? 1 : ((8 / VPL) > L ? L : (8 / VPL))) : 1;
+    // slots per batch: 8 vectors per lane per batch (4 for FP8, whose decoded
+    // vectors are 4x wider); two batches are in flight with the pipelining
+    static constexpr int VB = (DT == KPP_FP8_E4M3) ? 4 : 8;
+    static constexpr int JB = WIDE ? ((VB / VPL) < 1 ? 1 : ((VB / VPL) > L ? L : (VB / VPL))) : 1;
     static_assert(!WIDE || (RB % 16 == 0), "wide rows are whole vectors");
     static_assert(!WIDE || (VPR % L == 0 && L >= 1 && L <= 32 && (L & (L - 1)) == 0),
                   "lanes per row must divide the row's vectors");
@@ -184,8 +186,10 @@ __device__ __forceinline__ float update_d2(const PassIO &io, int64_t row, float 
 }
 
 // One pass over rows [r0, r1) by all warps of the CTA, each over its own
-// segment.  Writes the warp's segment sum and returns it (identical on all
-// lanes of the warp).
+// segment.  Loads are software-pipelined: the vectors of the next batch of
+// rows are requested before the current batch is computed, so every warp
+// keeps memory requests in flight continuously.  Writes the warp's segment
+// sum and returns it (identical on all lanes of the warp).
 template <int DT, int D, int L_, int MODE>
 __device__ __forceinline__ Pair pass_rows(const PassIO &io, const CentreRegs<DT, D, L_> &cr)
 {
@@ -198,78 +202,121 @@ __device__ __forceinline__ Pair pass_rows(const PassIO &io, const CentreRegs<DT,
     const int64_t nsup = (seg_last - seg_first + G::SW - 1) / G::SW;
     Pair lacc{};
 
-    for (int64_t j = 0; j < nsup; ++j) {
+    // super-iteration j of this warp: first row and shared-memory cache slot
+    auto super_at = [&](int64_t j, int64_t &rb, char *&slot) {
         const int64_t jj = io.reverse ? (nsup - 1 - j) : j;
-        const int64_t rb = seg_first + jj * G::SW;
-        char *slot = (io.cache != nullptr && jj < io.cache_supers)
-                         ? io.cache + ((int64_t)warp * io.cache_supers + jj) * G::SW * G::RB
-                         : nullptr;
-        const char *from = io.fill_cache ? nullptr : slot;
-        char *store = io.fill_cache ? slot : nullptr;
-        float mine[G::RPV];
-        int64_t own_row;
-        if constexpr (G::WIDE) {
-            const int g = lane / G::L, l = lane % G::L;
-            mine[0] = 0.f;
-#pragma unroll 1
-            for (int jb = 0; jb < G::L; jb += G::JB) {
-                uint4 x[G::JB][G::VPL];
-                float sc[G::JB];
+        rb = seg_first + jj * G::SW;
+        slot = (io.cache != nullptr && jj < io.cache_supers)
+                   ? io.cache + ((int64_t)warp * io.cache_supers + jj) * G::SW * G::RB
+                   : nullptr;
+    };
+
+    if constexpr (G::WIDE) {
+        // batch bi = slots [jb, jb + JB) of super-iteration bi / NB
+        constexpr int NB = G::L / G::JB;
+        const int g = lane / G::L, l = lane % G::L;
+        const int64_t nbatch = nsup * NB;
+        using Vecs = uint4[G::JB][G::VPL];
+        using Scales = float[G::JB];
+        auto issue = [&](int64_t bi, Vecs &x, Scales &sc) {
+            int64_t rb;
+            char *slot;
+            super_at(bi / NB, rb, slot);
+            const int jb = (int)(bi % NB) * G::JB;
+            const char *from = io.fill_cache ? nullptr : slot;
+#pragma unroll
+            for (int q = 0; q < G::JB; ++q) {
+                const int64_t row = rb + (int64_t)(jb + q) * (32 / G::L) + g;
+                const bool ok = row < seg_last;
+                sc[q] = (DT == KPP_FP8_E4M3 && ok) ? __ldg(io.scales + row) : 1.0f;
+#pragma unroll
+                for (int v = 0; v < G::VPL; ++v)
+                    x[q][v] = ok ? load_vec(io, from, rb, row, (v * G::L + l) * 16, G::RB)
+                                 : make_uint4(0, 0, 0, 0);
+            }
+        };
+        float mine = 0.f;
+        auto consume = [&](int64_t bi, const Vecs &x, const Scales &sc) {
+            int64_t rb;
+            char *slot;
+            super_at(bi / NB, rb, slot);
+            const int jb = (int)(bi % NB) * G::JB;
+            if (io.fill_cache && slot) {
 #pragma unroll
                 for (int q = 0; q < G::JB; ++q) {
                     const int64_t row = rb + (int64_t)(jb + q) * (32 / G::L) + g;
-                    const bool ok = row < seg_last;
-                    sc[q] = (DT == KPP_FP8_E4M3 && ok) ? __ldg(io.scales + row) : 1.0f;
+                    if (row < seg_last) {
 #pragma unroll
-                    for (int v = 0; v < G::VPL; ++v)
-                        x[q][v] = ok ? load_vec(io, from, rb, row, (v * G::L + l) * 16, G::RB)
-                                     : make_uint4(0, 0, 0, 0);
-                }
-                if (store) {
-#pragma unroll
-                    for (int q = 0; q < G::JB; ++q) {
-                        const int64_t row = rb + (int64_t)(jb + q) * (32 / G::L) + g;
-                        if (row < seg_last) {
-#pragma unroll
-                            for (int v = 0; v < G::VPL; ++v)
-                                *reinterpret_cast<uint4 *>(store + (row - rb) * G::RB +
-                                                           (v * G::L + l) * 16) = x[q][v];
-                        }
+                        for (int v = 0; v < G::VPL; ++v)
+                            *reinterpret_cast<uint4 *>(slot + (row - rb) * G::RB +
+                                                       (v * G::L + l) * 16) = x[q][v];
                     }
-                }
-#pragma unroll
-                for (int q = 0; q < G::JB; ++q) {
-                    float a0 = 0.f, a1 = 0.f;
-#pragma unroll
-                    for (int v = 0; v < G::VPL; ++v) {
-                        float f[G::EPV];
-                        decode16<DT>(x[q][v], f);
-                        cr.template accum<G::EPV>(f, v * G::EPV, sc[q], a0, a1);
-                    }
-                    float part = a0 + a1;
-#pragma unroll
-                    for (int o = G::L / 2; o > 0; o >>= 1)
-                        part += __shfl_xor_sync(0xffffffffu, part, o);
-                    if (l == jb + q)
-                        mine[0] = part;
                 }
             }
-            own_row = rb + (int64_t)l * (32 / G::L) + g;
-        } else {
-            own_row = rb + (int64_t)lane * G::RPV;
+#pragma unroll
+            for (int q = 0; q < G::JB; ++q) {
+                float a0 = 0.f, a1 = 0.f;
+#pragma unroll
+                for (int v = 0; v < G::VPL; ++v) {
+                    float f[G::EPV];
+                    decode16<DT>(x[q][v], f);
+                    cr.template accum<G::EPV>(f, v * G::EPV, sc[q], a0, a1);
+                }
+                float part = a0 + a1;
+#pragma unroll
+                for (int o = G::L / 2; o > 0; o >>= 1)
+                    part += __shfl_xor_sync(0xffffffffu, part, o);
+                if (l == jb + q)
+                    mine = part;
+            }
+            if (jb + G::JB == G::L) { // last batch of the super-iteration
+                const int64_t own_row = rb + (int64_t)l * (32 / G::L) + g;
+                if (own_row < seg_last)
+                    lacc.add(update_d2<MODE>(io, own_row, mine));
+            }
+        };
+        Vecs xa, xb;
+        Scales sa, sb;
+        if (nbatch > 0)
+            issue(0, xa, sa);
+        for (int64_t bi = 0; bi < nbatch; bi += 2) {
+            if (bi + 1 < nbatch)
+                issue(bi + 1, xb, sb);
+            consume(bi, xa, sa);
+            if (bi + 1 < nbatch) {
+                if (bi + 2 < nbatch)
+                    issue(bi + 2, xa, sa);
+                consume(bi + 1, xb, sb);
+            }
+        }
+    } else {
+        // narrow rows: one 16-byte vector (RPV rows) per lane and super-iteration
+        auto issue = [&](int64_t j, uint4 &x) {
+            int64_t rb;
+            char *slot;
+            super_at(j, rb, slot);
+            const int64_t own = rb + (int64_t)lane * G::RPV;
+            x = (own + G::RPV <= seg_last)
+                    ? load_vec(io, io.fill_cache ? nullptr : slot, rb, own, 0, G::RB)
+                    : make_uint4(0, 0, 0, 0);
+        };
+        auto consume = [&](int64_t j, const uint4 &x) {
+            int64_t rb;
+            char *slot;
+            super_at(j, rb, slot);
+            const int64_t own_row = rb + (int64_t)lane * G::RPV;
             float f[G::EPV];
             float sc[G::RPV];
             if (own_row + G::RPV <= seg_last) {
-                uint4 x = load_vec(io, from, rb, own_row, 0, G::RB);
-                if (store)
-                    *reinterpret_cast<uint4 *>(store + (own_row - rb) * G::RB) = x;
+                if (io.fill_cache && slot)
+                    *reinterpret_cast<uint4 *>(slot + (own_row - rb) * G::RB) = x;
                 decode16<DT>(x, f);
 #pragma unroll
                 for (int r = 0; r < G::RPV; ++r)
                     sc[r] = (DT == KPP_FP8_E4M3) ? __ldg(io.scales + own_row + r) : 1.0f;
             } else {
                 // ragged tail of the segment: element loads from global memory,
-                // never past its end (the cache is not used for these rows)
+                // never past its end (these rows are never cached)
 #pragma unroll
                 for (int r = 0; r < G::RPV; ++r) {
                     const int64_t row = own_row + r;
@@ -284,14 +331,23 @@ __device__ __forceinline__ Pair pass_rows(const PassIO &io, const CentreRegs<DT,
             for (int r = 0; r < G::RPV; ++r) {
                 float a0 = 0.f, a1 = 0.f;
                 cr.template accum<D>(f + r * D, r * D, sc[r], a0, a1);
-                mine[r] = a0 + a1;
+                const int64_t row = own_row + r;
+                if (row < seg_last)
+                    lacc.add(update_d2<MODE>(io, row, a0 + a1));
             }
-        }
-#pragma unroll
-        for (int r = 0; r < G::RPV; ++r) {
-            const int64_t row = own_row + r;
-            if (row < seg_last)
-                lacc.add(update_d2<MODE>(io, row, mine[r]));
+        };
+        uint4 xa, xb;
+        if (nsup > 0)
+            issue(0, xa);
+        for (int64_t j = 0; j < nsup; j += 2) {
+            if (j + 1 < nsup)
+                issue(j + 1, xb);
+            consume(j, xa);
+            if (j + 1 < nsup) {
+                if (j + 2 < nsup)
+                    issue(j + 2, xa);
+                consume(j + 1, xb);
+            }
         }
     }
     const Pair seg = warp_pair_sum(lacc);

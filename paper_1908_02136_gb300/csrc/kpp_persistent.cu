@@ -27,17 +27,16 @@ namespace kpp {
 
 constexpr int kPersistThreads = 512;
 constexpr int kPersistWarps = kPersistThreads / 32;
+constexpr int kMaxBlocks = 640;    // grid limit of the persistent form
+constexpr int kMaxChunks = 1024;   // 32-row chunks per block searched directly
 
 struct DrawShared {
-    float2 stage_pairs[kStage]; // level 1: block sums of the pass
-    float stage_rows[kStage];   // level 3: D^2 of the owner's segment
-    RowsShared rows;
-    Pair before;   // prefix before the owner block / segment
-    double u;      // draw of the next seed
-    double t;      // threshold u * T
+    float2 stage_pairs[kMaxBlocks]; // level 1: block sums of the pass
+    Pair before;                    // prefix before the owner block
+    Thresh th[2];                   // thresholds of the draws, by parity
+    Thresh th_draw;                 // the threshold of this pass's draw, with T
     double T;
     int64_t owner; // winning block, or -1 (degenerate: T == 0)
-    int64_t seg;
     int64_t pick;
     int ok;
 };
@@ -55,9 +54,13 @@ __global__ void __launch_bounds__(kPersistThreads, 1)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t r0 = (int64_t)b * p.chunk;
     const int64_t r1 = (r0 + p.chunk) < p.N ? (r0 + p.chunk) : p.N;
+    // dynamic shared memory: [point cache][D^2 of the block][32-row chunk sums]
     char *cache = a.cache_supers > 0 ? smem : nullptr;
     const int64_t cache_bytes = a.cache_supers * (int64_t)kPersistWarps * G::SW * G::RB;
     float *d2s = reinterpret_cast<float *>(smem + cache_bytes);
+    float2 *chunk_sums = reinterpret_cast<float2 *>(smem + cache_bytes + ((4 * p.chunk + 15) & ~15ll));
+    const int nchunks = (int)((r1 - r0 + 31) / 32);
+    const bool chunk_path = (MODE == D2_SMEM) && (p.chunk + 31) / 32 <= kMaxChunks;
     const uint64_t policy =
         a.l2_hint == 1 ? policy_evict_last() : (a.l2_hint == 2 ? policy_evict_first() : 0ull);
 
@@ -67,17 +70,18 @@ __global__ void __launch_bounds__(kPersistThreads, 1)
             atomicCAS(&p.ctl->status, KPP_OK, KPP_ERR_INVALID_ARG);
         return; // every CTA takes this branch: nobody is left waiting
     }
-    if (b == 0 && threadIdx.x == 0)
-        p.idx[0] = ci;
+    if (threadIdx.x == 0) {
+        if (b == 0)
+            p.idx[0] = ci;
+        if (p.K > 1)
+            ds.th[1] = thresh_for_u(philox_uniform(p.seed, p.stream_id, 1));
+    }
 
     for (int m = 0; m < p.K; ++m) {
         const bool last = (m == p.K - 1);
         const int next = m + 1;
         CentreRegs<DT, D, L> cr;
         cr.load(p.points, p.scales, ci);
-        // the next draw's uniform, by a thread that has time to spare
-        if (threadIdx.x == blockDim.x - 1 && !last)
-            ds.u = philox_uniform(p.seed, p.stream_id, (uint64_t)next);
 
         PassIO io{};
         io.r0 = r0;
@@ -104,36 +108,71 @@ __global__ void __launch_bounds__(kPersistThreads, 1)
             for (int w = 0; w < kPersistWarps; ++w)
                 bs.add(Pair{segsum[w].x, segsum[w].y});
             st_relaxed_u64(slots + (size_t)b * kSlotWords, pack_slot(bs, m));
-            ds.ok = 1;
         }
         if (last && b != 0)
             return; // only block 0 waits, to sum phi
-        __syncthreads();
+        const bool forced = !last && next < p.n_forced;
 
-        // wait for every block's sum of this pass (the grid-wide sync)
-        for (int k = threadIdx.x; k < p.nblocks; k += blockDim.x) {
-            Pair v;
-            if (wait_slot(slots + (size_t)k * kSlotWords, m, p.ctl, a.timeout_ns, &v))
-                ds.stage_pairs[k] = make_float2(v.hi, v.lo);
-            else
-                ds.ok = 0;
-        }
-        __syncthreads();
-        if (!ds.ok)
-            return;
-
-        if (last) { // block 0: phi = the ordered sum of the final block sums
-            if (warp == 0) {
+        if (warp == 0) {
+            // wait for every block's sum of this pass (the grid-wide sync),
+            // then the draw's first level: the block holding t = u * T
+            bool ok = true;
+            for (int k0 = 0; ok && k0 < p.nblocks; k0 += 256) {
+                const int n = (p.nblocks - k0) < 256 ? (p.nblocks - k0) : 256;
+                ok = warp_wait_slots(slots + (size_t)k0 * kSlotWords, n, m, p.ctl, a.timeout_ns,
+                                     ds.stage_pairs + k0);
+            }
+            __syncwarp();
+            if (ok && last) { // block 0: phi = the ordered sum of the final block sums
                 const PFind r = warp_pfind(
                     p.nblocks,
                     [&](int k) { return Pair{ds.stage_pairs[k].x, ds.stage_pairs[k].y}; },
-                    Pair{}, INFINITY, false);
+                    Pair{}, thresh_inf(), false);
                 if (lane == 0 && p.phi)
                     p.phi[0] = (double)r.total.hi + (double)r.total.lo;
+            } else if (ok && !forced) {
+                const PFind r = warp_pfind(
+                    p.nblocks,
+                    [&](int k) { return Pair{ds.stage_pairs[k].x, ds.stage_pairs[k].y}; },
+                    Pair{}, ds.th[next & 1], true);
+                if (lane == 0) {
+                    ds.th_draw = r.th;
+                    if (!(r.total.hi > 0.f)) {
+                        ds.owner = -1;
+                        ds.T = 0.0;
+                    } else if (r.index >= 0) {
+                        ds.owner = r.index;
+                        ds.before = r.before;
+                    } else { // rounding left no block above t: the last with weight
+                        ds.owner = r.last_positive;
+                        ds.before = Pair{};
+                        ds.th_draw.inf = 1;
+                    }
+                }
             }
-            return;
+            if (lane == 0)
+                ds.ok = ok ? 1 : 0;
+        } else if (!last) {
+            // meanwhile: the uniform of the draw after next, and this block's
+            // 32-row chunk sums (for the owner's search below)
+            if (threadIdx.x == 32 && next + 1 < p.K)
+                ds.th[(next + 1) & 1] =
+                    thresh_for_u(philox_uniform(p.seed, p.stream_id, (uint64_t)(next + 1)));
+            if (chunk_path && !forced) {
+                for (int c = threadIdx.x - 32; c < nchunks; c += blockDim.x - 32) {
+                    const int64_t rb = r0 + 32ll * c;
+                    const int n = (int)((r1 - rb) < 32 ? (r1 - rb) : 32);
+                    Pair cs{};
+                    for (int k = 0; k < n; ++k)
+                        cs.add(d2s[rb - r0 + k]);
+                    chunk_sums[c] = make_float2(cs.hi, cs.lo);
+                }
+            }
         }
-        if (next < p.n_forced) {
+        __syncthreads();
+        if (!ds.ok || last)
+            return;
+        if (forced) {
             ci = p.forced[next];
             if (ci < 0 || ci >= p.N) {
                 if (b == 0 && threadIdx.x == 0)
@@ -144,29 +183,6 @@ __global__ void __launch_bounds__(kPersistThreads, 1)
                 p.idx[next] = ci;
             continue;
         }
-
-        // level 1, on every CTA: the block holding t = u * T
-        if (warp == 0) {
-            const PFind r = warp_pfind(
-                p.nblocks,
-                [&](int k) { return Pair{ds.stage_pairs[k].x, ds.stage_pairs[k].y}; }, Pair{},
-                ds.u, true);
-            if (lane == 0) {
-                ds.T = (double)r.total.hi + (double)r.total.lo;
-                ds.t = r.t;
-                if (!(ds.T > 0.0)) {
-                    ds.owner = -1;
-                } else if (r.index >= 0) {
-                    ds.owner = r.index;
-                    ds.before = r.before;
-                } else { // rounding left no block above t: the last with weight
-                    ds.owner = r.last_positive;
-                    ds.before = Pair{};
-                    ds.t = INFINITY;
-                }
-            }
-        }
-        __syncthreads();
         const int64_t owner = ds.owner;
         if (owner < 0) {
             // sum D^2 == 0: fewer distinct points than K.  This pass's D^2 is
@@ -178,47 +194,66 @@ __global__ void __launch_bounds__(kPersistThreads, 1)
                 for (int k = next; k < p.K; ++k)
                     p.idx[k] = -1;
                 if (p.phi)
-                    p.phi[0] = ds.T;
+                    p.phi[0] = 0.0;
                 atomicCAS(&p.ctl->status, KPP_OK, KPP_ERR_DEGENERATE);
             }
             return;
         }
 
         if (owner == b) {
-            // levels 2 and 3 from this CTA's own memory: the segment, then the row
+            // the point within this block, from its own shared memory, by
+            // warp 0; then publish the index
             if (warp == 0) {
-                const PFind r = warp_pfind(
-                    kPersistWarps, [&](int k) { return Pair{segsum[k].x, segsum[k].y}; },
-                    ds.before, ds.t, false);
-                if (lane == 0) {
+                const Pair base = ds.before;
+                Thresh t = ds.th_draw;
+                int64_t pick;
+                if (chunk_path) {
+                    // the 32-row chunk, then the row
+                    const PFind r = warp_pfind(
+                        nchunks, [&](int k) { return Pair{chunk_sums[k].x, chunk_sums[k].y}; },
+                        base, t, false);
+                    int c;
+                    Pair before = r.before;
                     if (r.index >= 0) {
-                        ds.seg = r.index;
-                        ds.before = r.before;
+                        c = (int)r.index;
                     } else {
-                        ds.seg = r.last_positive >= 0 ? r.last_positive : 0;
-                        ds.t = INFINITY;
+                        c = r.last_positive >= 0 ? (int)r.last_positive : 0;
+                        t.inf = 1;
                     }
+                    const int64_t rb = r0 + 32ll * c;
+                    const int n = (int)((r1 - rb) < 32 ? (r1 - rb) : 32);
+                    const float v = lane < n ? d2s[rb - r0 + lane] : 0.f;
+                    const Find32 f = warp_find32(n, Pair{v, 0.f}, before, t);
+                    pick = rb + (f.index >= 0 ? f.index : 0);
+                } else {
+                    // the warp segment, then the row
+                    const PFind r = warp_pfind(
+                        kPersistWarps, [&](int k) { return Pair{segsum[k].x, segsum[k].y}; },
+                        base, t, false);
+                    Pair sbase = base;
+                    int seg;
+                    if (r.index >= 0) {
+                        seg = (int)r.index;
+                        sbase = r.before;
+                    } else { // rounding: the last segment with weight
+                        seg = r.last_positive >= 0 ? (int)r.last_positive : 0;
+                        t.inf = 1;
+                    }
+                    int64_t first, lastr;
+                    segment_rows(r0, r1 - r0, G::SW, kPersistWarps, seg, &first, &lastr);
+                    if (MODE == D2_SMEM)
+                        pick = warp_rows_find(
+                            first, lastr, [&](int64_t row) { return d2s[row - r0]; }, sbase, t);
+                    else
+                        pick = warp_rows_find(
+                            first, lastr, [&](int64_t row) { return p.d2[row]; }, sbase, t);
                 }
-            }
-            __syncthreads();
-            int64_t first, lastr;
-            segment_rows(r0, r1 - r0, G::SW, kPersistWarps, (int)ds.seg, &first, &lastr);
-            const Pair base = ds.before;
-            const double t = ds.t;
-            int64_t pick;
-            if (MODE == D2_SMEM)
-                pick = block_rows_find(
-                    first, lastr, [&](int64_t row) { return d2s[row - r0]; }, base, t,
-                    ds.stage_rows, &ds.rows);
-            else
-                pick = block_rows_find(
-                    first, lastr, [&](int64_t row) { return p.d2[row]; }, base, t,
-                    ds.stage_rows, &ds.rows);
-            if (threadIdx.x == 0) {
-                p.idx[next] = pick;
-                st_relaxed_u64(&p.ctl->mail, ((unsigned long long)pick << 32) |
-                                                 (unsigned long long)(uint32_t)next);
-                ds.pick = pick;
+                if (lane == 0) {
+                    p.idx[next] = pick;
+                    st_relaxed_u64(&p.ctl->mail, ((unsigned long long)pick << 32) |
+                                                     (unsigned long long)(uint32_t)next);
+                    ds.pick = pick;
+                }
             }
         } else if (threadIdx.x == 0) {
             ds.pick = wait_mail(p.ctl, m, a.timeout_ns);
@@ -292,6 +327,7 @@ bool persistent_lookup(int dt, int d, int lanes, PersistentKernel *out)
 }
 
 int persistent_threads() { return kPersistThreads; }
+int persistent_max_blocks() { return kMaxBlocks; }
 int persistent_segments() { return kPersistWarps; }
 
 cudaError_t persistent_launch(const void *fn, int grid, size_t smem, const Problem &p,

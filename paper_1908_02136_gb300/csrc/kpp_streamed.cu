@@ -37,12 +37,11 @@ __device__ __forceinline__ void finish_pass(const Problem &p, int m, const Pair 
 {
     __shared__ float2 segsum[kStreamThreads / 32];
     __shared__ float2 stage_pairs[kStage];
-    __shared__ float stage_rows[kStage];
-    __shared__ RowsShared rows;
     __shared__ int is_last;
     __shared__ int64_t blk_sh, seg_sh;
     __shared__ Pair before_sh;
-    __shared__ double t_sh, T_sh;
+    __shared__ Thresh th_sh;
+    __shared__ double T_sh;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (lane == 0)
         segsum[warp] = make_float2(wseg.hi, wseg.lo);
@@ -70,17 +69,17 @@ __device__ __forceinline__ void finish_pass(const Problem &p, int m, const Pair 
         const double u = (final_pass || forced) ? 0.0
                                                 : philox_uniform(p.seed, p.stream_id, (uint64_t)next);
         const PFind r = warp_pfind(
-            p.nblocks, [&](int k) { return Pair{stage_pairs[k].x, stage_pairs[k].y}; }, Pair{}, u,
-            true);
+            p.nblocks, [&](int k) { return Pair{stage_pairs[k].x, stage_pairs[k].y}; }, Pair{},
+            thresh_for_u(u), true);
         if (lane == 0) {
             T_sh = (double)r.total.hi + (double)r.total.lo;
-            t_sh = r.t;
+            th_sh = r.th;
             blk_sh = r.index;
             before_sh = r.before;
             if (r.index < 0) { // rounding left no block above t: the last with weight
                 blk_sh = r.last_positive;
                 before_sh = Pair{};
-                t_sh = INFINITY;
+                th_sh.inf = 1;
             }
         }
     }
@@ -114,23 +113,24 @@ __device__ __forceinline__ void finish_pass(const Problem &p, int m, const Pair 
                 const float2 v = __ldcg(segs + k);
                 return Pair{v.x, v.y};
             },
-            before_sh, t_sh, false);
+            before_sh, th_sh, false);
         if (lane == 0) {
             if (r.index >= 0) {
                 seg_sh = r.index;
                 before_sh = r.before;
             } else {
                 seg_sh = r.last_positive >= 0 ? r.last_positive : 0;
-                t_sh = INFINITY;
+                th_sh.inf = 1;
             }
         }
     }
     __syncthreads();
+    if (warp != 0)
+        return;
     int64_t first, last;
     segment_rows(row0, rows_blk, p.sw, p.nseg, (int)seg_sh, &first, &last);
-    const int64_t pick = block_rows_find(
-        first, last, [&](int64_t row) { return __ldcg(p.d2 + row); }, before_sh, t_sh,
-        stage_rows, &rows);
+    const int64_t pick = warp_rows_find(
+        first, last, [&](int64_t row) { return __ldcg(p.d2 + row); }, before_sh, th_sh);
     if (threadIdx.x == 0) {
         p.idx[next] = pick;
         p.ctl->ticket = 0u; // ready for the next launch
