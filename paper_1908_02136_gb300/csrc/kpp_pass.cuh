@@ -43,6 +43,35 @@ struct Geom {
     static_assert(!WIDE || (L % JB == 0), "slot batches tile the slots");
 };
 
+// Packed FP32 pairs for the Blackwell FP32x2 instructions.
+using F2 = unsigned long long;
+
+__device__ __forceinline__ F2 f2(float lo, float hi)
+{
+    F2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+
+__device__ __forceinline__ void f2_split(F2 v, float &lo, float &hi)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+
+__device__ __forceinline__ F2 f2_sub(F2 a, F2 b)
+{
+    F2 r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+
+__device__ __forceinline__ F2 f2_fma(F2 a, F2 b, F2 c)
+{
+    F2 r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+
 // Per-lane slice of the newest centre, decoded to FP32 once per pass.  For
 // FP8 each coordinate is the pair (c_hi, c_lo) of split_fp8_centre.
 template <int DT, int D, int L_>
@@ -87,25 +116,28 @@ struct CentreRegs {
         }
     }
 
-    // Adds sum_e (x_e - c_{k0+e})^2 of one decoded vector into (a0, a1).
+    // Adds sum_e (x_e - c_{k0+e})^2 of one decoded vector into (a0, a1):
+    // even elements into a0, odd into a1, with packed FP32x2 instructions
+    // (each lane of a packed op rounds exactly like the scalar op).
     // `s` is the row scale (FP8 only).
     template <int N>
     __device__ __forceinline__ void accum(const float *f, int k0, float s, float &a0,
                                           float &a1) const
     {
+        F2 acc = f2(a0, a1);
 #pragma unroll
         for (int e = 0; e < N; e += 2) {
-            float t0, t1;
+            F2 t;
             if constexpr (DT == KPP_FP8_E4M3) {
-                t0 = diff_fp8(s, f[e], c[k0 + e], clo[k0 + e]);
-                t1 = diff_fp8(s, f[e + 1], c[k0 + e + 1], clo[k0 + e + 1]);
+                const F2 x = f2_fma(f2(s, s), f2(f[e], f[e + 1]),
+                                    f2(-c[k0 + e], -c[k0 + e + 1]));
+                t = f2_sub(x, f2(clo[k0 + e], clo[k0 + e + 1]));
             } else {
-                t0 = f[e] - c[k0 + e];
-                t1 = f[e + 1] - c[k0 + e + 1];
+                t = f2_sub(f2(f[e], f[e + 1]), f2(c[k0 + e], c[k0 + e + 1]));
             }
-            a0 = fmaf(t0, t0, a0);
-            a1 = fmaf(t1, t1, a1);
+            acc = f2_fma(t, t, acc);
         }
+        f2_split(acc, a0, a1);
     }
 };
 
@@ -155,13 +187,34 @@ __device__ __forceinline__ uint64_t policy_evict_first()
     return p;
 }
 
+// 16-byte shared-memory accesses by explicit shared-window address (the
+// cache pointer is chosen at run time between shared and global memory, so
+// the compiler could not prove the address space by itself).
+__device__ __forceinline__ uint4 lds16(const void *p)
+{
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+    uint4 v;
+    asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "r"(a));
+    return v;
+}
+
+__device__ __forceinline__ void sts16(void *p, uint4 v)
+{
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+    asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(a), "r"(v.x), "r"(v.y),
+                 "r"(v.z), "r"(v.w)
+                 : "memory");
+}
+
 // One 16-byte vector of row data: from the shared-memory cache slot of the
 // super-iteration (if cached and not being filled), else from global memory.
 __device__ __forceinline__ uint4 load_vec(const PassIO &io, const char *cslot, int64_t rb,
                                           int64_t row, int byte_in_row, int RB)
 {
     if (cslot)
-        return *reinterpret_cast<const uint4 *>(cslot + (row - rb) * RB + byte_in_row);
+        return lds16(cslot + (row - rb) * RB + byte_in_row);
     const char *g = io.gpts + row * RB + byte_in_row;
     return io.policy ? ld_global_hint(g, io.policy) : ld_stream16(g);
 }
@@ -224,9 +277,35 @@ __device__ __forceinline__ Pair pass_rows(const PassIO &io, const CentreRegs<DT,
             super_at(bi / NB, rb, slot);
             const int jb = (int)(bi % NB) * G::JB;
             const char *from = io.fill_cache ? nullptr : slot;
+            const int64_t row0 = rb + (int64_t)jb * (32 / G::L) + g; // row of slot jb
+            constexpr int QB = (32 / G::L) * G::RB;                   // bytes between slots
+            if (rb + G::SW <= seg_last) {
+                // whole super-iteration in range: no bounds checks, one base
+                // address and immediate offsets
+                if (from) {
+                    const char *p0 = from + (row0 - rb) * G::RB + l * 16;
+#pragma unroll
+                    for (int q = 0; q < G::JB; ++q)
+#pragma unroll
+                        for (int v = 0; v < G::VPL; ++v)
+                            x[q][v] = lds16(p0 + q * QB + v * G::L * 16);
+                } else {
+                    const char *p0 = io.gpts + row0 * G::RB + l * 16;
+#pragma unroll
+                    for (int q = 0; q < G::JB; ++q)
+#pragma unroll
+                        for (int v = 0; v < G::VPL; ++v)
+                            x[q][v] = io.policy ? ld_global_hint(p0 + q * QB + v * G::L * 16, io.policy)
+                                                : ld_stream16(p0 + q * QB + v * G::L * 16);
+                }
+#pragma unroll
+                for (int q = 0; q < G::JB; ++q)
+                    sc[q] = (DT == KPP_FP8_E4M3) ? __ldg(io.scales + row0 + q * (32 / G::L)) : 1.0f;
+                return;
+            }
 #pragma unroll
             for (int q = 0; q < G::JB; ++q) {
-                const int64_t row = rb + (int64_t)(jb + q) * (32 / G::L) + g;
+                const int64_t row = row0 + (int64_t)q * (32 / G::L);
                 const bool ok = row < seg_last;
                 sc[q] = (DT == KPP_FP8_E4M3 && ok) ? __ldg(io.scales + row) : 1.0f;
 #pragma unroll
@@ -248,8 +327,7 @@ __device__ __forceinline__ Pair pass_rows(const PassIO &io, const CentreRegs<DT,
                     if (row < seg_last) {
 #pragma unroll
                         for (int v = 0; v < G::VPL; ++v)
-                            *reinterpret_cast<uint4 *>(slot + (row - rb) * G::RB +
-                                                       (v * G::L + l) * 16) = x[q][v];
+                            sts16(slot + (row - rb) * G::RB + (v * G::L + l) * 16, x[q][v]);
                     }
                 }
             }
@@ -309,7 +387,7 @@ __device__ __forceinline__ Pair pass_rows(const PassIO &io, const CentreRegs<DT,
             float sc[G::RPV];
             if (own_row + G::RPV <= seg_last) {
                 if (io.fill_cache && slot)
-                    *reinterpret_cast<uint4 *>(slot + (own_row - rb) * G::RB) = x;
+                    sts16(slot + (own_row - rb) * G::RB, x);
                 decode16<DT>(x, f);
 #pragma unroll
                 for (int r = 0; r < G::RPV; ++r)
