@@ -63,6 +63,43 @@ def dist_env():
     return rank, world, local
 
 
+def kernel_source_hash():
+    """SHA-256 over the CUDA sources and the C header (to tell whether a
+    committed ncu traffic figure still describes the kernel being run)."""
+    import glob
+    import hashlib
+
+    h = hashlib.sha256()
+    files = sorted(glob.glob(os.path.join(ROOT, "paper_1908_02136_gb300", "csrc", "*")))
+    files.append(os.path.join(ROOT, "include", "kpp.h"))
+    for f in files:
+        h.update(os.path.basename(f).encode())
+        h.update(open(f, "rb").read())
+    return h.hexdigest()
+
+
+def profiled_traffic(workload: str, dtype: str):
+    """DRAM bytes per launch from the committed ncu summary of this workload,
+    or None if there is none or the kernel sources changed since."""
+    path = os.path.join(ROOT, "profiles", f"persistent_kernel_{workload}_{dtype}.md")
+    try:
+        txt = open(path).read()
+    except OSError:
+        return None
+    fields = {}
+    for line in txt.splitlines():
+        if ":" in line and line.split(":", 1)[0] in ("traffic_bytes_per_launch",
+                                                     "kernel_source_sha256"):
+            k, v = line.split(":", 1)
+            fields[k] = v.strip()
+    if fields.get("kernel_source_sha256") != kernel_source_hash():
+        return None
+    try:
+        return int(fields["traffic_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
 def measured_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -326,8 +363,9 @@ def main():
     d2_bytes = 8 * N if form_name == "streamed" else 0  # D^2 stays on chip when persistent
     alg_bytes = passes_per_launch * (point_bytes + d2_bytes)
     achieved = alg_bytes / (per_launch_ms / 1e3) / 1e9
+    traffic = profiled_traffic(wl.name, args.dtype) if form_name == "persistent" else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak, "traffic": traffic,
                 "peak_source": "measured" if peaks else "fallback",
                 "kernel": f"{form_name}_kernel", "algorithmic_bytes_per_launch": alg_bytes,
                 "algorithmic_bytes_per_pass": point_bytes + d2_bytes}
