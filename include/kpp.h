@@ -206,6 +206,44 @@ KPP_API kpp_status kpp_quantize(const float *x, int64_t N, int32_t d, kpp_dtype 
                         float *row_scales, kpp_stream_t stream);
 
 /*
+ * Batching form (not in the paper): many independent seedings -- of uneven
+ * N, d and K, all stored as `dtype` -- in one cooperative launch.  Each
+ * problem is exactly the kpp_seed problem (same draws for the same seed and
+ * stream id, same results up to the blocking of the prefix sums).
+ * Problems costing more than one SM's share of the batch run on a team of
+ * CTAs; the others on one CTA each, longest first, from a work queue.
+ * d must be one of 2, 4, 8, 16, 32, 64, 128 (KPP_ERR_UNSUPPORTED otherwise).
+ */
+typedef struct {
+    const void *points;      /* [N x d] device, 16-byte aligned */
+    const float *row_scales; /* [N] FP8 only, else NULL */
+    int64_t N;
+    int32_t d;
+    int32_t K;
+    uint64_t seed;
+    uint64_t stream_id;
+    int64_t *indices_out; /* [K] device */
+    float *d2_out;        /* [N] device */
+    double *phi_out;      /* [1] device, or NULL */
+} kpp_problem;
+
+/* Workspace bytes kpp_seed_batched needs for this HOST array of problems
+ * on the current device (0 if the problems are invalid). */
+KPP_API size_t kpp_batch_workspace_size(const kpp_problem *problems, int32_t n, kpp_dtype dtype,
+                                        const kpp_options *opts);
+
+/*
+ * Seeds every problem of the HOST array `problems` (read during the call;
+ * the device buffers it points to must stay valid until the work is done).
+ * Asynchronous on `stream`.  Device outcomes: kpp_read_status(workspace)
+ * gives the first non-OK status of any problem (a degenerate problem does
+ * not stop the others; its indices end with -1).
+ */
+KPP_API kpp_status kpp_seed_batched(const kpp_problem *problems, int32_t n, kpp_dtype dtype,
+                                    void *workspace, size_t workspace_bytes, kpp_stream_t stream,
+                                    const kpp_options *opts);
+
+/*
  * Seeding for callers that cannot allocate device memory.  (The paper has
  * no counterpart; this is a calling convention of this library.)
  *

@@ -63,6 +63,16 @@ class Plan(ctypes.Structure):
         return {name: getattr(self, name) for name, _ in self._fields_}
 
 
+class Problem(ctypes.Structure):
+    """Mirror of kpp_problem."""
+
+    _fields_ = [("points", ctypes.c_void_p), ("row_scales", ctypes.c_void_p),
+                ("N", ctypes.c_int64), ("d", ctypes.c_int32), ("K", ctypes.c_int32),
+                ("seed", ctypes.c_uint64), ("stream_id", ctypes.c_uint64),
+                ("indices_out", ctypes.c_void_p), ("d2_out", ctypes.c_void_p),
+                ("phi_out", ctypes.c_void_p)]
+
+
 _lock = threading.Lock()
 _lib = None
 
@@ -99,6 +109,10 @@ def load_library(build_if_stale: bool = True):
         lib.kpp_seed_noalloc.argtypes = [P, P, I64, I32, I32, ctypes.c_int, U64, U64, P, P, P,
                                          P, P, P]
         lib.kpp_seed_noalloc.restype = ctypes.c_int
+        lib.kpp_batch_workspace_size.argtypes = [P, I32, ctypes.c_int, P]
+        lib.kpp_batch_workspace_size.restype = ctypes.c_size_t
+        lib.kpp_seed_batched.argtypes = [P, I32, ctypes.c_int, P, ctypes.c_size_t, P, P]
+        lib.kpp_seed_batched.restype = ctypes.c_int
         lib.kpp_read_status.argtypes = [P, P]
         lib.kpp_read_status.restype = ctypes.c_int
         lib.kpp_quantize.argtypes = [P, I64, I32, ctypes.c_int, P, P, P]
@@ -168,6 +182,15 @@ def kpp_seed_noalloc(points, row_scales, N, d, K, dtype, seed, stream_id, indice
     return load_library().kpp_seed_noalloc(points, row_scales, N, d, K, dtype, seed, stream_id,
                                            indices_out, d2_out, phi_out, stream,
                                            _opts_ptr(opts), ds)
+
+
+def kpp_batch_workspace_size(problems, n, dtype, opts=None) -> int:
+    return load_library().kpp_batch_workspace_size(problems, n, dtype, _opts_ptr(opts))
+
+
+def kpp_seed_batched(problems, n, dtype, workspace, workspace_bytes, stream, opts=None) -> int:
+    return load_library().kpp_seed_batched(problems, n, dtype, workspace, workspace_bytes,
+                                           stream, _opts_ptr(opts))
 
 
 def kpp_read_status(workspace, stream) -> int:
@@ -314,3 +337,51 @@ def quantize(x, to: str, *, out=None, row_scales=None):
     if st != OK:
         raise KppError(st, "kpp_quantize")
     return q if s is None else (q, s)
+
+
+def seed_batched(points_list, Ks, seeds, stream_ids=None, *, dtype=None, row_scales=None,
+                 opts=None, outs=None, workspace=None, check: bool = True):
+    """Batched seeding through ``kpp_seed_batched``.
+
+    ``points_list``: CUDA tensors [N_p, d_p] (same storage type); ``Ks``,
+    ``seeds``, ``stream_ids``: per-problem ints.  Returns a list of
+    ``(idx, d2, phi)`` and the workspace (reusable for the same batch).
+    """
+    import torch
+
+    n = len(points_list)
+    dev = points_list[0].device
+    dt = _dtype_code(points_list[0], dtype)
+    stream_ids = list(range(n)) if stream_ids is None else stream_ids
+    if outs is None:
+        outs = [(torch.empty(K, dtype=torch.int64, device=dev),
+                 torch.empty(x.shape[0], dtype=torch.float32, device=dev),
+                 torch.empty(1, dtype=torch.float64, device=dev))
+                for x, K in zip(points_list, Ks)]
+    arr = (Problem * n)()
+    for i, (x, K) in enumerate(zip(points_list, Ks)):
+        idx, d2, phi = outs[i]
+        arr[i].points = x.data_ptr()
+        arr[i].row_scales = None if row_scales is None else row_scales[i].data_ptr()
+        arr[i].N = x.shape[0]
+        arr[i].d = x.shape[1]
+        arr[i].K = int(K)
+        arr[i].seed = int(seeds[i])
+        arr[i].stream_id = int(stream_ids[i])
+        arr[i].indices_out = idx.data_ptr()
+        arr[i].d2_out = d2.data_ptr()
+        arr[i].phi_out = phi.data_ptr()
+    with torch.cuda.device(dev):
+        if workspace is None:
+            # 0 means the problems are rejected; kpp_seed_batched reports why
+            nb = kpp_batch_workspace_size(arr, n, dt, opts)
+            workspace = torch.empty(max(nb, 256), dtype=torch.uint8, device=dev)
+        st = kpp_seed_batched(arr, n, dt, workspace.data_ptr(), workspace.numel(),
+                              _stream_handle(dev), opts)
+        if st != OK:
+            raise KppError(st, "kpp_seed_batched")
+        if check:
+            st = kpp_read_status(workspace.data_ptr(), _stream_handle(dev))
+            if st != OK:
+                raise KppError(st, "kpp_seed_batched (device)")
+    return outs, workspace

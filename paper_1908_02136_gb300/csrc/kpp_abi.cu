@@ -440,6 +440,7 @@ kpp_status kpp_seed(const void *points, const float *row_scales, int64_t N, int3
     p.ctl = reinterpret_cast<Control *>(ws);
     if (pl.form == KPP_FORM_PERSISTENT) {
         p.slots = reinterpret_cast<unsigned long long *>(ws + pl.off_slots);
+        p.mail = &p.ctl->mail;
     } else {
         p.block_sums = reinterpret_cast<float2 *>(ws + pl.off_bsum);
         p.seg_sums = reinterpret_cast<float2 *>(ws + pl.off_seg);

@@ -53,6 +53,7 @@ struct Problem {
     float2 *block_sums; // streamed form: [nblocks] pair sums of the pass
     float2 *seg_sums;   // streamed form: [nblocks * nseg] pair sums of the pass
     unsigned long long *slots; // persistent form: [2][nblocks * kSlotWords] tagged block sums
+    unsigned long long *mail;  // persistent form: the drawn index, tagged with its pass
 };
 
 // ---------------------------------------------------------------------------
@@ -663,11 +664,12 @@ __device__ __forceinline__ bool warp_wait_slots(const unsigned long long *slots,
 }
 
 // Waits until the mailbox carries pass m's index; returns it, or -1.
-__device__ __forceinline__ int64_t wait_mail(Control *ctl, int m, uint64_t timeout_ns)
+__device__ __forceinline__ int64_t wait_mail(const unsigned long long *mail, Control *ctl, int m,
+                                             uint64_t timeout_ns)
 {
     const uint64_t t0 = global_ns();
     for (uint32_t it = 1;; ++it) {
-        const unsigned long long w = ld_relaxed_u64(&ctl->mail);
+        const unsigned long long w = ld_relaxed_u64(mail);
         if ((uint32_t)w == (uint32_t)(m + 1))
             return (int64_t)(w >> 32);
         if (give_up(ctl, t0, timeout_ns, it, (uint32_t)m))

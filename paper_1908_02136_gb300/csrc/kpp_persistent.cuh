@@ -43,16 +43,25 @@ struct DrawShared {
     int ok;
 };
 
+// Static shared state of one CTA running seed_blocks.
+struct BlockShared {
+    float2 segsum[kPersistWarps];
+    DrawShared ds;
+};
+
+// The seeding of problem p by a team of p.nblocks co-resident CTAs, this CTA
+// being member b: p.slots and p.mail are the team's own exchange words.
+// `smem` is the CTA's dynamic shared memory (point cache, D^2, chunk sums;
+// unused when a.cache_supers == 0 and MODE == D2_INPLACE).  Returns when the
+// seeding is done, or early -- the same way on every member -- on an error
+// recorded in the status word.
 template <int DT, int D, int L, int MODE>
-__global__ void __launch_bounds__(kPersistThreads, 1)
-    persistent_kernel(Problem p, PersistArgs a)
+__device__ __forceinline__ void seed_blocks(const Problem &p, const PersistArgs &a, const int b,
+                                            char *smem, BlockShared &sh)
 {
     using G = Geom<DT, D, L>;
-    extern __shared__ __align__(16) char smem[];
-    __shared__ float2 segsum[kPersistWarps];
-    __shared__ DrawShared ds;
-
-    const int b = blockIdx.x;
+    float2 *segsum = sh.segsum;
+    DrawShared &ds = sh.ds;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t r0 = (int64_t)b * p.chunk;
     const int64_t r1 = (r0 + p.chunk) < p.N ? (r0 + p.chunk) : p.N;
@@ -110,6 +119,8 @@ __global__ void __launch_bounds__(kPersistThreads, 1)
             for (int w = 0; w < kPersistWarps; ++w)
                 bs.add(Pair{segsum[w].x, segsum[w].y});
             st_relaxed_u64(slots + (size_t)b * kSlotWords, pack_slot(bs, m));
+            if (p.nblocks == 1) // alone: this block's sum is level 1
+                ds.stage_pairs[0] = make_float2(bs.hi, bs.lo);
         }
         if (last && b != 0)
             return; // only block 0 waits, to sum phi
@@ -119,7 +130,7 @@ __global__ void __launch_bounds__(kPersistThreads, 1)
             // wait for every block's sum of this pass (the grid-wide sync),
             // then the draw's first level: the block holding t = u * T
             bool ok = true;
-            for (int k0 = 0; ok && k0 < p.nblocks; k0 += 256) {
+            for (int k0 = 0; ok && p.nblocks > 1 && k0 < p.nblocks; k0 += 256) {
                 const int n = (p.nblocks - k0) < 256 ? (p.nblocks - k0) : 256;
                 ok = warp_wait_slots(slots + (size_t)k0 * kSlotWords, n, m, p.ctl, a.timeout_ns,
                                      ds.stage_pairs + k0);
@@ -252,19 +263,28 @@ __global__ void __launch_bounds__(kPersistThreads, 1)
                 }
                 if (lane == 0) {
                     p.idx[next] = pick;
-                    st_relaxed_u64(&p.ctl->mail, ((unsigned long long)pick << 32) |
-                                                     (unsigned long long)(uint32_t)next);
+                    st_relaxed_u64(p.mail, ((unsigned long long)pick << 32) |
+                                                 (unsigned long long)(uint32_t)next);
                     ds.pick = pick;
                 }
             }
         } else if (threadIdx.x == 0) {
-            ds.pick = wait_mail(p.ctl, m, a.timeout_ns);
+            ds.pick = wait_mail(p.mail, p.ctl, m, a.timeout_ns);
         }
         __syncthreads();
         ci = ds.pick;
         if (ci < 0)
             return; // a wait gave up: the status word says why
     }
+}
+
+template <int DT, int D, int L, int MODE>
+__global__ void __launch_bounds__(kPersistThreads, 1)
+    persistent_kernel(Problem p, PersistArgs a)
+{
+    extern __shared__ __align__(16) char smem[];
+    __shared__ BlockShared sh;
+    seed_blocks<DT, D, L, MODE>(p, a, blockIdx.x, smem, sh);
 }
 
 // One specialisation of the persistent kernel, as listed by the per-dtype

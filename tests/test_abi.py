@@ -29,7 +29,8 @@ def lib():
 def test_header_declares_the_boundary():
     names = declared_entry_points()
     for required in ["kpp_seed", "kpp_workspace_size", "kpp_read_status", "kpp_quantize",
-                     "kpp_seed_host", "kpp_status_string", "kpp_version", "kpp_describe"]:
+                     "kpp_seed_host", "kpp_status_string", "kpp_version", "kpp_describe",
+                     "kpp_seed_batched", "kpp_batch_workspace_size", "kpp_seed_noalloc"]:
         assert required in names
 
 
@@ -77,7 +78,8 @@ def test_ctypes_structs_match_the_header(tmp_path):
 
     src = tmp_path / "layout.c"
     lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "kpp.h"', "int main(void){"]
-    for cname, py in (("kpp_options", kpp.Options), ("kpp_plan", kpp.Plan)):
+    for cname, py in (("kpp_options", kpp.Options), ("kpp_plan", kpp.Plan),
+                      ("kpp_problem", kpp.Problem)):
         lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
         for f, _ in py._fields_:
             lines.append(f'printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
@@ -88,7 +90,8 @@ def test_ctypes_structs_match_the_header(tmp_path):
                    check=True)
     out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
     got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
-    for cname, py in (("kpp_options", kpp.Options), ("kpp_plan", kpp.Plan)):
+    for cname, py in (("kpp_options", kpp.Options), ("kpp_plan", kpp.Plan),
+                      ("kpp_problem", kpp.Problem)):
         assert got[(cname, "size")] == ctypes.sizeof(py)
         for f, _ in py._fields_:
             assert got[(cname, f)] == getattr(py, f).offset, (cname, f)
