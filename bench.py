@@ -34,6 +34,7 @@ sys.path.insert(0, ROOT)
 METRIC = "k-means++ seeding ms & N·K·d/s; HBM GB/s vs peak; BF16/batched vs FP32"
 UNIT = "N*K*d/s"
 DEFAULT_WORKLOAD = "gmm-N1e6-d32-K256"
+BATCH_WORKLOAD = "batch-512"
 
 
 def parse():
@@ -53,6 +54,8 @@ def parse():
     ap.add_argument("--min-rows", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-phi", action="store_true")
+    ap.add_argument("--no-sequential", action="store_true")
     return ap.parse_args()
 
 
@@ -216,6 +219,125 @@ def run_reference(args, rank, world):
     }), flush=True)
 
 
+def run_batch(args, rank, world, dev, pg, barrier):
+    """The 512-problem batch: one kpp_seed_batched launch per step, against the
+    same problems seeded one kpp_seed call after another (the plain path)."""
+    import ctypes
+
+    import numpy as np
+    import torch
+
+    import paper_1908_02136_gb300 as kpp
+    from paper_1908_02136_gb300 import datagen
+
+    table = datagen.batch_table()
+    xs = [torch.from_numpy(datagen.batch_problem_points(pr)).to(dev) for pr in table]
+    Ks = [pr.K for pr in table]
+    streams = [pr.p + 512 * rank for pr in table]
+    seeds = [1] * len(table)
+    stream = torch.cuda.Stream(dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    nkd = float(sum(pr.N * pr.K * pr.d for pr in table))
+    alg_bytes = float(sum(pr.N * pr.K * pr.d * 4 for pr in table))
+    with torch.cuda.stream(stream):
+        outs, ws = kpp.seed_batched(xs, Ks, seeds, streams, check=True)
+        sh = ctypes.c_void_p(stream.cuda_stream)
+        arr = (kpp.Problem * len(table))()
+        for i, (x, K) in enumerate(zip(xs, Ks)):
+            idx, d2, phi = outs[i]
+            arr[i].points, arr[i].row_scales = x.data_ptr(), None
+            arr[i].N, arr[i].d, arr[i].K = x.shape[0], x.shape[1], K
+            arr[i].seed, arr[i].stream_id = 1, streams[i]
+            arr[i].indices_out, arr[i].d2_out, arr[i].phi_out = (idx.data_ptr(), d2.data_ptr(),
+                                                                 phi.data_ptr())
+
+        def launch():
+            st = kpp.kpp_seed_batched(arr, len(table), kpp.F32, ws.data_ptr(), ws.numel(), sh)
+            if st != kpp.OK:
+                raise kpp.KppError(st, "kpp_seed_batched")
+
+        for _ in range(args.warmup):
+            flush.fill_(1)
+            launch()
+        st = kpp.kpp_read_status(ws.data_ptr(), sh)
+        if st != kpp.OK:
+            raise kpp.KppError(st, "warmup")
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        torch.cuda.synchronize(dev)
+        barrier()
+        sampler = ClockSampler(int(str(dev).split(":")[-1]) if ":" in str(dev) else 0)
+        sampler.start()
+        time.sleep(0.3)
+        for s_ in range(args.steps):
+            flush.fill_(s_ & 0xFF)
+            starts[s_].record(stream)
+            launch()
+            ends[s_].record(stream)
+        torch.cuda.synchronize(dev)
+        clocks = sampler.stop()
+        barrier()
+        step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
+        # the plain path: one kpp_seed per problem, back to back
+        seq_ms = None
+        if not args.no_sequential:
+            wss = [kpp.workspace_for(x.shape[0], x.shape[1], K, kpp.F32, dev)
+                   for x, K in zip(xs, Ks)]
+            o2 = [(torch.empty(K, dtype=torch.int64, device=dev),
+                   torch.empty(x.shape[0], dtype=torch.float32, device=dev),
+                   torch.empty(1, dtype=torch.float64, device=dev)) for x, K in zip(xs, Ks)]
+
+            def seq():
+                for i, (x, K) in enumerate(zip(xs, Ks)):
+                    st = kpp.kpp_seed(x.data_ptr(), None, x.shape[0], x.shape[1], K, kpp.F32, 1,
+                                      streams[i], None, 0, o2[i][0].data_ptr(),
+                                      o2[i][1].data_ptr(), o2[i][2].data_ptr(), wss[i].data_ptr(),
+                                      wss[i].numel(), sh)
+                    if st != kpp.OK:
+                        raise kpp.KppError(st, "kpp_seed")
+
+            seq()
+            torch.cuda.synchronize(dev)
+            a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            flush.fill_(2)
+            a_.record(stream)
+            seq()
+            b_.record(stream)
+            torch.cuda.synchronize(dev)
+            seq_ms = a_.elapsed_time(b_)
+    total_ms = sum(step_ms)
+    if pg is not None:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms = total_ms / args.steps
+    for (idx, d2, phi), pr in zip(outs, table):
+        ih = idx.cpu().numpy()
+        assert np.all((ih >= 0) & (ih < pr.N)) and len(set(ih.tolist())) == pr.K
+    peaks = measured_peaks()
+    peak = peaks["hbm_gbs"] if peaks else 6800.0
+    achieved = alg_bytes / (ms / 1e3) / 1e9
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": nkd * world * args.steps / (total_ms / 1e3), "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": BATCH_WORKLOAD, "problems": len(table), "sum_NKd": nkd,
+                       "form": "batched", "parallelism": f"replicas{world}",
+                       "l2": "flushed between steps (512 MiB write)",
+                       "plain_sequential_ms": seq_ms,
+                       "batched_speedup_vs_plain": (seq_ms / ms) if seq_ms else None},
+            "clocks": clocks, "e2e": None,
+            # one cooperative launch per distinct d (wave) per step
+            "gpu_launches": args.steps * len({pr.d for pr in table}),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "kernel": "batched_kernel",
+                         "algorithmic_bytes_per_launch": alg_bytes},
+            "cpu_baseline": None,
+        }), flush=True)
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -242,6 +364,9 @@ def main():
         if pg is not None:
             pg.barrier()
 
+    if args.workload == BATCH_WORKLOAD:
+        run_batch(args, rank, world, dev, pg, barrier)
+        return
     wl = datagen.WORKLOADS[args.workload]
     x_np = datagen.workload_points(wl) if wl.N <= 2_000_000 else None
     x = torch.from_numpy(x_np).to(dev) if x_np is not None else datagen.workload_points(wl, dev)
@@ -323,6 +448,22 @@ def main():
     assert np.all((idx_h >= 0) & (idx_h < N)) and len(set(idx_h.tolist())) == K
     assert float(d2[idx].abs().max()) == 0.0
 
+    # precision forms: cost of this form's seeds on the original FP32 points,
+    # evaluated by replaying its indices through the FP32 path
+    precision = None
+    if args.dtype != "f32" and not args.no_phi:
+        with torch.cuda.stream(stream):
+            phi_form = float(phi.item())
+            _, _, phi_orig = kpp.seed(x, K, seed, stream_id, forced=idx.clone(), check=True)
+            i32, _, phi32 = kpp.seed(x, K, seed, stream_id, check=True)
+            torch.cuda.synchronize(dev)
+        phi_orig = float(phi_orig.item())
+        phi32 = float(phi32.item())
+        precision = {"phi_form_own": phi_form, "phi_of_form_seeds_on_fp32_points": phi_orig,
+                     "phi_rel_diff": abs(phi_form - phi_orig) / phi_orig,
+                     "phi_fp32_same_seed": phi32,
+                     "phi_vs_fp32_run": (phi_orig - phi32) / phi32}
+
     # e2e: host points (pinned) -> C ABI -> host results, wall clock incl. copies
     e2e = None
     if not args.no_e2e:
@@ -398,6 +539,7 @@ def main():
                        "l2": "flushed between steps (512 MiB write)",
                        "step_ms_min": min(step_ms), "step_ms_max": max(step_ms)},
             "clocks": clocks, "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
+            "precision": precision,
             "roofline": roofline, "cpu_baseline": cpu_baseline,
         }), flush=True)
     if pg is not None:

@@ -1,17 +1,9 @@
-// kpp_batched.cu -- host side of the batching form: the schedule (teams for
-// the costly problems, an LPT queue for the rest), the workspace and the
-// launch.  Kernel in kpp_batched.cuh.
-//
-// The host sorts the problems by cost (K * N * d * bytes) and splits them in
-// two classes.  A problem costing more than one SM's fair share of the whole
-// batch gets a team of CTAs sized in proportion to its cost; the team runs it
-// exactly like the persistent form (seed_blocks: per-warp segments, tagged
-// block-sum slots and mailbox local to the team).  Every other problem is
-// seeded by a single CTA: CTAs outside the teams -- and team members once
-// their team's problem is done -- take the next problem from an atomic queue
-// in decreasing order of cost (longest processing time first).  D^2 stays in
-// each problem's output array; every problem has its own control block, so
-// one problem's degenerate data does not stop the others.
+// kpp_batched.cu -- host side of the batching form: problems grouped into
+// waves by d; per wave, team sizes from cost, the static list schedule of
+// the team jobs (longest first, each on the CTAs free earliest) and the queue
+// of single-CTA jobs; the workspace and the launches.  Kernel in
+// kpp_batched.cuh.
+
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -23,15 +15,15 @@ namespace kpp {
 
 namespace {
 
-BatchFn batched_fn(int dt)
+BatchFn batched_fn(int dt, int d)
 {
     switch (dt) {
     case KPP_F32:
-        return batched_kernel_f32();
+        return batched_kernel_f32(d);
     case KPP_BF16:
-        return batched_kernel_bf16();
+        return batched_kernel_bf16(d);
     default:
-        return batched_kernel_fp8();
+        return batched_kernel_fp8(d);
     }
 }
 
@@ -71,15 +63,25 @@ int batch_rows_per_super(int dt, int d)
 constexpr size_t kAlign = 256;
 size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
+// The problems of one d and their schedule on the grid.
+struct Wave {
+    int d;
+    BatchFn fn;
+    std::vector<std::vector<BatchEntry>> lists; // team jobs per CTA, in schedule order
+    std::vector<int32_t> queue;                  // single-CTA jobs, longest first
+    size_t nentries;
+    size_t off_entries, off_first, off_queue, off_counter; // workspace offsets
+};
+
 struct BatchPlan {
     int grid;
-    std::vector<int> order;     // problem index of job j
-    std::vector<int> team_size; // for big jobs
-    std::vector<int> team_first;
-    int nbig;
+    std::vector<int> team;    // team size of each problem (by problem index)
+    std::vector<int> nblocks; // CTAs that own rows (<= team)
+    std::vector<int64_t> chunk;
+    std::vector<Wave> waves; // launched in this order
     // workspace layout
-    size_t off_jobs, off_ctls, off_cta_job, off_team_slots, off_solo_slots, bytes;
-    std::vector<size_t> team_slot_off; // per big job, relative to off_team_slots
+    size_t off_jobs, off_ctls, off_slots, bytes;
+    std::vector<size_t> slot_off; // per problem, relative to off_slots
 };
 
 int elem_bytes(int dt) { return dt == KPP_F32 ? 4 : dt == KPP_BF16 ? 2 : 1; }
@@ -116,69 +118,119 @@ kpp_status make_batch_plan(const kpp_problem *pr, int32_t n, int dt, const kpp_o
         return KPP_ERR_CUDA;
     if (!coop)
         return KPP_ERR_UNSUPPORTED;
-    int resident = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, (const void *)batched_fn(dt),
-                                                      kPersistThreads, 0) != cudaSuccess)
-        return KPP_ERR_CUDA;
-    if (resident < 1)
-        return KPP_ERR_UNSUPPORTED;
     const int grid = sms; // one CTA per SM
     const int64_t min_rows = (opts && opts->min_rows_per_cta > 0) ? opts->min_rows_per_cta : 2048;
     const double eb = elem_bytes(dt);
-    // cost in bytes read, plus a per-pass cost for the exchange of a team
-    std::vector<double> cost(n);
-    double total = 0;
-    for (int i = 0; i < n; ++i) {
-        cost[i] = (double)pr[i].K * ((double)pr[i].N * pr[i].d * eb + 256.0 * 1024.0);
-        total += cost[i];
-    }
-    std::vector<int> idx(n);
+    // Cost model, in bytes-equivalents: the points read per pass, D^2 read and
+    // written per pass, and a fixed per-pass cost of the exchange.
+    auto cost_of = [&](int i, int t) {
+        const double rows = (double)pr[i].N / t;
+        return (double)pr[i].K * (rows * (pr[i].d * eb + 8.0) + (t > 1 ? 256.0e3 : 64.0e3));
+    };
+    std::vector<double> c1(n);
     for (int i = 0; i < n; ++i)
-        idx[i] = i;
-    std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) { return cost[x] > cost[y]; });
-    const double share = total / grid;
+        c1[i] = cost_of(i, 1);
     bp->grid = grid;
-    bp->order.clear();
-    bp->team_size.clear();
-    bp->team_first.clear();
-    int used = 0;
-    std::vector<int> small;
-    for (int i : idx) {
-        int t = (int)std::lround(cost[i] / share);
-        const int64_t tmax = (pr[i].N + min_rows - 1) / min_rows;
-        if (t > tmax)
-            t = (int)tmax;
-        if (t >= 2 && used + t <= grid) {
-            bp->order.push_back(i);
-            bp->team_size.push_back(t);
-            bp->team_first.push_back(used);
-            used += t;
-        } else {
-            small.push_back(i);
+    bp->team.assign(n, 1);
+    bp->nblocks.assign(n, 1);
+    bp->chunk.assign(n, 0);
+    bp->waves.clear();
+    static const int kDims[] = {2, 4, 8, 16, 32, 64, 128};
+    std::vector<int> order;
+    std::vector<double> avail(grid);
+    std::vector<int> cta(grid);
+    for (int d : kDims) {
+        order.clear();
+        double total = 0;
+        for (int i = 0; i < n; ++i)
+            if (pr[i].d == d) {
+                order.push_back(i);
+                total += c1[i];
+            }
+        if (order.empty())
+            continue;
+        Wave w;
+        w.d = d;
+        w.fn = batched_fn(dt, d);
+        int resident = 0;
+        if (!w.fn ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, (const void *)w.fn,
+                                                          kPersistThreads, 0) != cudaSuccess)
+            return KPP_ERR_CUDA;
+        if (resident < 1)
+            return KPP_ERR_UNSUPPORTED;
+        const double share = total / grid;
+        std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return c1[x] > c1[y]; });
+        w.lists.assign(grid, {});
+        // list scheduling: each team problem, longest first, takes the t CTAs
+        // that are free earliest; all of them start it when the last of them
+        // is free
+        std::fill(avail.begin(), avail.end(), 0.0);
+        for (int i : order) {
+            int t = (int)std::ceil(c1[i] / share);
+            const int64_t tmax = (pr[i].N + min_rows - 1) / min_rows;
+            if (t > tmax)
+                t = (int)tmax;
+            if (t < 1)
+                t = 1;
+            if (t > grid)
+                t = grid;
+            const int64_t sw = batch_rows_per_super(dt, d);
+            int64_t chunk = (pr[i].N + t - 1) / t;
+            chunk = (chunk + sw - 1) / sw * sw;
+            const int nb = (int)((pr[i].N + chunk - 1) / chunk);
+            bp->team[i] = t;
+            bp->nblocks[i] = nb;
+            bp->chunk[i] = chunk;
+            if (nb == 1) { // served by the queue
+                w.queue.push_back(i);
+                continue;
+            }
+            for (int c = 0; c < grid; ++c)
+                cta[c] = c;
+            std::partial_sort(cta.begin(), cta.begin() + nb, cta.end(), [&](int x, int y) {
+                return avail[x] < avail[y] || (avail[x] == avail[y] && x < y);
+            });
+            double start = 0;
+            for (int r = 0; r < nb; ++r)
+                start = std::max(start, avail[cta[r]]);
+            const double fin = start + cost_of(i, nb);
+            for (int r = 0; r < nb; ++r) {
+                avail[cta[r]] = fin;
+                w.lists[cta[r]].push_back(BatchEntry{i, r});
+            }
         }
+        w.nentries = 0;
+        for (auto &l : w.lists)
+            w.nentries += l.size();
+        bp->waves.push_back(std::move(w));
     }
-    bp->nbig = (int)bp->order.size();
-    for (int i : small)
-        bp->order.push_back(i);
-    // workspace: batch control | job table | job control blocks | cta_job |
-    //            team slots (+ team mailbox word) | solo slots
+    // workspace: batch control | job table | job control blocks |
+    //            per wave: entries, list offsets, queue, queue counter |
+    //            every problem's slots
     size_t off = sizeof(Control);
     bp->off_jobs = off;
     off += round_up(sizeof(BatchJob) * (size_t)n, kAlign);
     bp->off_ctls = off;
     off += round_up(sizeof(Control) * (size_t)n, kAlign);
-    bp->off_cta_job = off;
-    off += round_up(sizeof(int32_t) * (size_t)grid, kAlign);
-    bp->off_team_slots = off;
-    bp->team_slot_off.clear();
-    size_t toff = 0;
-    for (int j = 0; j < bp->nbig; ++j) {
-        bp->team_slot_off.push_back(toff);
-        toff += round_up(8 * (2 * kSlotWords * (size_t)bp->team_size[j]), kAlign);
+    for (Wave &w : bp->waves) {
+        w.off_entries = off;
+        off += round_up(sizeof(BatchEntry) * w.nentries, kAlign);
+        w.off_first = off;
+        off += round_up(sizeof(int32_t) * (size_t)(grid + 1), kAlign);
+        w.off_queue = off;
+        off += round_up(sizeof(int32_t) * (w.queue.size() + 1), kAlign);
+        w.off_counter = off;
+        off += kAlign;
     }
-    off += toff;
-    bp->off_solo_slots = off;
-    off += round_up(8 * 2 * kSlotWords * (size_t)grid, kAlign);
+    bp->off_slots = off;
+    bp->slot_off.assign(n, 0);
+    size_t soff = 0;
+    for (int i = 0; i < n; ++i) {
+        bp->slot_off[i] = soff;
+        soff += round_up(8 * 2 * kSlotWords * (size_t)bp->nblocks[i], 64);
+    }
+    off += round_up(soff, kAlign);
     bp->bytes = off;
     return KPP_OK;
 }
@@ -213,13 +265,12 @@ kpp_status kpp_seed_batched(const kpp_problem *problems, int32_t n, kpp_dtype dt
         return KPP_ERR_WORKSPACE;
     char *ws = reinterpret_cast<char *>(workspace);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    // host image of the job table and the CTA map
+    // host image of the job table and the work lists
     std::vector<BatchJob> jobs(n);
-    std::vector<int32_t> cta_job(bp.grid, -1);
     Control *ctls = reinterpret_cast<Control *>(ws + bp.off_ctls);
-    for (int j = 0; j < n; ++j) {
-        const kpp_problem &q = problems[bp.order[j]];
-        BatchJob &b = jobs[j];
+    for (int i = 0; i < n; ++i) {
+        const kpp_problem &q = problems[i];
+        BatchJob &b = jobs[i];
         std::memset(&b, 0, sizeof(b));
         Problem &p = b.p;
         p.points = q.points;
@@ -232,50 +283,62 @@ kpp_status kpp_seed_batched(const kpp_problem *problems, int32_t n, kpp_dtype dt
         p.idx = q.indices_out;
         p.d2 = q.d2_out;
         p.phi = q.phi_out;
-        p.ctl = ctls + j;
+        p.ctl = ctls + i;
+        p.mail = &p.ctl->mail;
         p.nseg = kPersistWarps;
         p.sw = batch_rows_per_super(dt, q.d);
+        p.chunk = bp.chunk[i];
+        p.nblocks = bp.nblocks[i];
+        p.slots = reinterpret_cast<unsigned long long *>(ws + bp.off_slots + bp.slot_off[i]);
         b.d = q.d;
-        const int t = j < bp.nbig ? bp.team_size[j] : 1;
-        int64_t chunk = (q.N + t - 1) / t;
-        chunk = (chunk + p.sw - 1) / p.sw * p.sw;
-        p.chunk = chunk;
-        p.nblocks = (int)((q.N + chunk - 1) / chunk);
-        p.mail = &p.ctl->mail;
-        if (j < bp.nbig) {
-            b.team_first = bp.team_first[j];
-            p.slots = reinterpret_cast<unsigned long long *>(ws + bp.off_team_slots +
-                                                               bp.team_slot_off[j]);
-            for (int r = 0; r < p.nblocks; ++r)
-                cta_job[b.team_first + r] = j;
-        } else {
-            b.team_first = -1;
-            p.slots = nullptr; // set per CTA on the device
-        }
     }
     if (cudaMemsetAsync(ws, 0, bp.bytes, s) != cudaSuccess ||
         cudaMemcpyAsync(ws + bp.off_jobs, jobs.data(), sizeof(BatchJob) * (size_t)n,
-                        cudaMemcpyHostToDevice, s) != cudaSuccess ||
-        cudaMemcpyAsync(ws + bp.off_cta_job, cta_job.data(), sizeof(int32_t) * (size_t)bp.grid,
                         cudaMemcpyHostToDevice, s) != cudaSuccess)
         return KPP_ERR_CUDA;
-    BatchArgs a;
-    std::memset(&a, 0, sizeof(a));
-    a.jobs = reinterpret_cast<const BatchJob *>(ws + bp.off_jobs);
-    a.njobs = n;
-    a.nbig = bp.nbig;
-    a.cta_job = reinterpret_cast<const int32_t *>(ws + bp.off_cta_job);
-    a.ctl = reinterpret_cast<Control *>(ws);
-    a.queue = &a.ctl->ticket;
-    a.solo_slots = reinterpret_cast<unsigned long long *>(ws + bp.off_solo_slots);
-    a.pa.cache_supers = 0;
-    a.pa.reverse = (opts && opts->alternate < 0) ? 0 : 1;
-    a.pa.l2_hint = (opts && opts->l2_policy == -1) ? 0 : ((opts && opts->l2_policy == 2) ? 2 : 1);
-    a.pa.timeout_ns = 1000ull * ((opts && opts->timeout_us) ? opts->timeout_us : 2000000u);
-    void *args[] = {&a};
-    if (cudaLaunchCooperativeKernel((const void *)batched_fn(dt), dim3(bp.grid),
-                                    dim3(kPersistThreads), args, 0, s) != cudaSuccess)
-        return KPP_ERR_LAUNCH;
+    // the lists and queues of every wave, in one staging image
+    const size_t lo = bp.waves.empty() ? bp.off_slots : bp.waves.front().off_entries;
+    std::vector<char> image(bp.off_slots - lo, 0);
+    for (const Wave &w : bp.waves) {
+        BatchEntry *ent = reinterpret_cast<BatchEntry *>(image.data() + (w.off_entries - lo));
+        int32_t *first = reinterpret_cast<int32_t *>(image.data() + (w.off_first - lo));
+        int32_t k = 0;
+        for (int c = 0; c < bp.grid; ++c) {
+            first[c] = k;
+            for (const BatchEntry &e : w.lists[c])
+                ent[k++] = e;
+        }
+        first[bp.grid] = k;
+        if (!w.queue.empty())
+            std::memcpy(image.data() + (w.off_queue - lo), w.queue.data(),
+                        sizeof(int32_t) * w.queue.size());
+    }
+    // (a copy from pageable memory has read its source when it returns)
+    if (!image.empty() && cudaMemcpyAsync(ws + lo, image.data(), image.size(),
+                                          cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return KPP_ERR_CUDA;
+    PersistArgs pa;
+    std::memset(&pa, 0, sizeof(pa));
+    pa.cache_supers = 0;
+    pa.reverse = (opts && opts->alternate < 0) ? 0 : 1;
+    pa.l2_hint = (opts && opts->l2_policy == -1) ? 0 : ((opts && opts->l2_policy == 2) ? 2 : 1);
+    pa.timeout_ns = 1000ull * ((opts && opts->timeout_us) ? opts->timeout_us : 2000000u);
+    for (const Wave &w : bp.waves) {
+        BatchArgs a;
+        std::memset(&a, 0, sizeof(a));
+        a.jobs = reinterpret_cast<const BatchJob *>(ws + bp.off_jobs);
+        a.entries = reinterpret_cast<const BatchEntry *>(ws + w.off_entries);
+        a.first = reinterpret_cast<const int32_t *>(ws + w.off_first);
+        a.queue_jobs = reinterpret_cast<const int32_t *>(ws + w.off_queue);
+        a.nqueue = (int32_t)w.queue.size();
+        a.queue = reinterpret_cast<unsigned int *>(ws + w.off_counter);
+        a.ctl = reinterpret_cast<Control *>(ws);
+        a.pa = pa;
+        void *args[] = {&a};
+        if (cudaLaunchCooperativeKernel((const void *)w.fn, dim3(bp.grid), dim3(kPersistThreads),
+                                        args, 0, s) != cudaSuccess)
+            return KPP_ERR_LAUNCH;
+    }
     return KPP_OK;
 }
 

@@ -1,8 +1,8 @@
-// kpp_batched_f32.cu -- batched-form kernel for F32 points.
+// kpp_batched_f32.cu -- batched-form wave kernels for F32 points, one per d.
 #include "kpp_batched.cuh"
 
 namespace kpp {
 
-BatchFn batched_kernel_f32() { return &batched_kernel<KPP_F32>; }
+BatchFn batched_kernel_f32(int d) { return batched_kernel_of<KPP_F32>(d); }
 
 } // namespace kpp

@@ -1,8 +1,8 @@
-// kpp_batched_fp8.cu -- batched-form kernel for FP8 points.
+// kpp_batched_fp8.cu -- batched-form wave kernels for FP8 points, one per d.
 #include "kpp_batched.cuh"
 
 namespace kpp {
 
-BatchFn batched_kernel_fp8() { return &batched_kernel<KPP_FP8_E4M3>; }
+BatchFn batched_kernel_fp8(int d) { return batched_kernel_of<KPP_FP8_E4M3>(d); }
 
 } // namespace kpp

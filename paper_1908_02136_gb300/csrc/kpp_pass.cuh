@@ -41,6 +41,13 @@ struct Geom {
                   "lanes per row must divide the row's vectors");
     static_assert(WIDE || (16 % RB == 0), "narrow rows tile a vector");
     static_assert(!WIDE || (L % JB == 0), "slot batches tile the slots");
+    // batches kept in flight by the software pipeline: about 16 vectors per
+    // lane whatever the row size (FP8: 8); narrow rows, which also carry
+    // RPV prefetched D^2 values per batch, 8 batches at most
+    static constexpr int VPB = WIDE ? JB * VPL : 1; // vectors per batch
+    static constexpr int PD0 = (2 * VB) / VPB;
+    static constexpr int PDW = PD0 < 2 ? 2 : (PD0 > 16 ? 16 : PD0);
+    static constexpr int PD = WIDE ? PDW : (RPV <= 2 ? 8 : (RPV == 4 ? 4 : 2));
 };
 
 // Packed FP32 pairs for the Blackwell FP32x2 instructions.
@@ -219,15 +226,27 @@ __device__ __forceinline__ uint4 load_vec(const PassIO &io, const char *cslot, i
     return io.policy ? ld_global_hint(g, io.policy) : ld_stream16(g);
 }
 
-// min-update of one owned row; returns the row's new D^2.
+// The previous D^2 of an owned row, for D2_INPLACE prefetched together with
+// the row's points (an L2 round trip that would otherwise stall the warp once
+// per super-iteration); unused in pass 0 and for D2_SMEM.
 template <int MODE>
-__device__ __forceinline__ float update_d2(const PassIO &io, int64_t row, float v)
+__device__ __forceinline__ float prefetch_d2(const PassIO &io, int64_t row, bool in_range)
+{
+    if (MODE != D2_INPLACE || io.first || !in_range)
+        return 0.f;
+    return __ldcg(io.d2 + row);
+}
+
+// min-update of one owned row; returns the row's new D^2.  `pre` is the
+// prefetched previous D^2 (D2_INPLACE).
+template <int MODE>
+__device__ __forceinline__ float update_d2(const PassIO &io, int64_t row, float v, float pre)
 {
     float *slot = (MODE == D2_INPLACE) ? io.d2 + row : io.d2s + (row - io.r0);
     if (io.first) {
         *slot = v;
     } else {
-        const float old = *slot;
+        const float old = (MODE == D2_INPLACE) ? pre : *slot;
         if (v < old)
             *slot = v;
         else
@@ -271,7 +290,7 @@ __device__ __forceinline__ Pair pass_rows(const PassIO &io, const CentreRegs<DT,
         const int64_t nbatch = nsup * NB;
         using Vecs = uint4[G::JB][G::VPL];
         using Scales = float[G::JB];
-        auto issue = [&](int64_t bi, Vecs &x, Scales &sc) {
+        auto issue = [&](int64_t bi, Vecs &x, Scales &sc, float &pre) {
             int64_t rb;
             char *slot;
             super_at(bi / NB, rb, slot);
@@ -279,6 +298,11 @@ __device__ __forceinline__ Pair pass_rows(const PassIO &io, const CentreRegs<DT,
             const char *from = io.fill_cache ? nullptr : slot;
             const int64_t row0 = rb + (int64_t)jb * (32 / G::L) + g; // row of slot jb
             constexpr int QB = (32 / G::L) * G::RB;                   // bytes between slots
+            pre = 0.f;
+            if (jb + G::JB == G::L) { // last batch: the own row's previous D^2
+                const int64_t own_row = rb + (int64_t)l * (32 / G::L) + g;
+                pre = prefetch_d2<MODE>(io, own_row, own_row < seg_last);
+            }
             if (rb + G::SW <= seg_last) {
                 // whole super-iteration in range: no bounds checks, one base
                 // address and immediate offsets
@@ -315,7 +339,7 @@ __device__ __forceinline__ Pair pass_rows(const PassIO &io, const CentreRegs<DT,
             }
         };
         float mine = 0.f;
-        auto consume = [&](int64_t bi, const Vecs &x, const Scales &sc) {
+        auto consume = [&](int64_t bi, const Vecs &x, const Scales &sc, float pre) {
             int64_t rb;
             char *slot;
             super_at(bi / NB, rb, slot);
@@ -350,26 +374,33 @@ __device__ __forceinline__ Pair pass_rows(const PassIO &io, const CentreRegs<DT,
             if (jb + G::JB == G::L) { // last batch of the super-iteration
                 const int64_t own_row = rb + (int64_t)l * (32 / G::L) + g;
                 if (own_row < seg_last)
-                    lacc.add(update_d2<MODE>(io, own_row, mine));
+                    lacc.add(update_d2<MODE>(io, own_row, mine, pre));
             }
         };
-        Vecs xa, xb;
-        Scales sa, sb;
-        if (nbatch > 0)
-            issue(0, xa, sa);
-        for (int64_t bi = 0; bi < nbatch; bi += 2) {
-            if (bi + 1 < nbatch)
-                issue(bi + 1, xb, sb);
-            consume(bi, xa, sa);
-            if (bi + 1 < nbatch) {
-                if (bi + 2 < nbatch)
-                    issue(bi + 2, xa, sa);
-                consume(bi + 1, xb, sb);
+        // ring of PD batches: batch bi + PD - 1 is requested before batch bi
+        // is computed
+        constexpr int P = G::PD;
+        Vecs x[P];
+        Scales sc[P];
+        float pre[P];
+#pragma unroll
+        for (int q = 0; q < P - 1; ++q)
+            if (q < nbatch)
+                issue(q, x[q], sc[q], pre[q]);
+        for (int64_t bi = 0; bi < nbatch; bi += P) {
+#pragma unroll
+            for (int q = 0; q < P; ++q) {
+                const int qn = (q + P - 1) % P;
+                if (bi + q + P - 1 < nbatch)
+                    issue(bi + q + P - 1, x[qn], sc[qn], pre[qn]);
+                if (bi + q < nbatch)
+                    consume(bi + q, x[q], sc[q], pre[q]);
             }
         }
     } else {
         // narrow rows: one 16-byte vector (RPV rows) per lane and super-iteration
-        auto issue = [&](int64_t j, uint4 &x) {
+        using Pre = float[G::RPV];
+        auto issue = [&](int64_t j, uint4 &x, Pre &pre) {
             int64_t rb;
             char *slot;
             super_at(j, rb, slot);
@@ -377,8 +408,11 @@ __device__ __forceinline__ Pair pass_rows(const PassIO &io, const CentreRegs<DT,
             x = (own + G::RPV <= seg_last)
                     ? load_vec(io, io.fill_cache ? nullptr : slot, rb, own, 0, G::RB)
                     : make_uint4(0, 0, 0, 0);
+#pragma unroll
+            for (int r = 0; r < G::RPV; ++r)
+                pre[r] = prefetch_d2<MODE>(io, own + r, own + r < seg_last);
         };
-        auto consume = [&](int64_t j, const uint4 &x) {
+        auto consume = [&](int64_t j, const uint4 &x, const Pre &pre) {
             int64_t rb;
             char *slot;
             super_at(j, rb, slot);
@@ -411,20 +445,24 @@ __device__ __forceinline__ Pair pass_rows(const PassIO &io, const CentreRegs<DT,
                 cr.template accum<D>(f + r * D, r * D, sc[r], a0, a1);
                 const int64_t row = own_row + r;
                 if (row < seg_last)
-                    lacc.add(update_d2<MODE>(io, row, a0 + a1));
+                    lacc.add(update_d2<MODE>(io, row, a0 + a1, pre[r]));
             }
         };
-        uint4 xa, xb;
-        if (nsup > 0)
-            issue(0, xa);
-        for (int64_t j = 0; j < nsup; j += 2) {
-            if (j + 1 < nsup)
-                issue(j + 1, xb);
-            consume(j, xa);
-            if (j + 1 < nsup) {
-                if (j + 2 < nsup)
-                    issue(j + 2, xa);
-                consume(j + 1, xb);
+        constexpr int P = G::PD;
+        uint4 x[P];
+        Pre pre[P];
+#pragma unroll
+        for (int q = 0; q < P - 1; ++q)
+            if (q < nsup)
+                issue(q, x[q], pre[q]);
+        for (int64_t j = 0; j < nsup; j += P) {
+#pragma unroll
+            for (int q = 0; q < P; ++q) {
+                const int qn = (q + P - 1) % P;
+                if (j + q + P - 1 < nsup)
+                    issue(j + q + P - 1, x[qn], pre[qn]);
+                if (j + q < nsup)
+                    consume(j + q, x[q], pre[q]);
             }
         }
     }
@@ -491,7 +529,7 @@ __device__ __forceinline__ Pair pass_rows_generic(const PassIO &io, int d, const
                                             : q0 - c_sh[k];
             a0 = fmaf(t0, t0, a0);
         }
-        lacc.add(update_d2<D2_INPLACE>(io, row, a0 + a1));
+        lacc.add(update_d2<D2_INPLACE>(io, row, a0 + a1, prefetch_d2<D2_INPLACE>(io, row, true)));
     }
     const Pair seg = warp_pair_sum(lacc);
     if (lane == 0)

@@ -41,6 +41,12 @@ struct DrawShared {
     int64_t owner; // winning block, or -1 (degenerate: T == 0)
     int64_t pick;
     int ok;
+    // the owner's search through a warp segment: its rows, the prefix before
+    // it, the threshold, and the sums of its kPersistWarps sub-slices
+    int64_t seg_first, seg_last;
+    Pair seg_before;
+    Thresh seg_th;
+    float2 subsum[kPersistWarps];
 };
 
 // Static shared state of one CTA running seed_blocks.
@@ -214,14 +220,14 @@ __device__ __forceinline__ void seed_blocks(const Problem &p, const PersistArgs 
         }
 
         if (owner == b) {
-            // the point within this block, from its own shared memory, by
-            // warp 0; then publish the index
-            if (warp == 0) {
-                const Pair base = ds.before;
-                Thresh t = ds.th_draw;
-                int64_t pick;
-                if (chunk_path) {
-                    // the 32-row chunk, then the row
+            // the point within this block; then publish the index
+            auto d2_at = [&](int64_t row) { return MODE == D2_SMEM ? d2s[row - r0] : p.d2[row]; };
+            int64_t pick = -1;
+            if (chunk_path) {
+                // from the 32-row chunk sums made during the wait, by warp 0
+                if (warp == 0) {
+                    const Pair base = ds.before;
+                    Thresh t = ds.th_draw;
                     const PFind r = warp_pfind(
                         nchunks, [&](int k) { return Pair{chunk_sums[k].x, chunk_sums[k].y}; },
                         base, t, false);
@@ -238,12 +244,17 @@ __device__ __forceinline__ void seed_blocks(const Problem &p, const PersistArgs 
                     const float v = lane < n ? d2s[rb - r0 + lane] : 0.f;
                     const Find32 f = warp_find32(n, Pair{v, 0.f}, before, t);
                     pick = rb + (f.index >= 0 ? f.index : 0);
-                } else {
-                    // the warp segment, then the row
+                }
+            } else {
+                // the warp segment (warp 0); the sums of its sub-slices of
+                // whole 32-row chunks, one per warp; the sub-slice and the
+                // row in it (warp 0)
+                if (warp == 0) {
+                    Thresh t = ds.th_draw;
                     const PFind r = warp_pfind(
                         kPersistWarps, [&](int k) { return Pair{segsum[k].x, segsum[k].y}; },
-                        base, t, false);
-                    Pair sbase = base;
+                        ds.before, t, false);
+                    Pair sbase = ds.before;
                     int seg;
                     if (r.index >= 0) {
                         seg = (int)r.index;
@@ -252,21 +263,52 @@ __device__ __forceinline__ void seed_blocks(const Problem &p, const PersistArgs 
                         seg = r.last_positive >= 0 ? (int)r.last_positive : 0;
                         t.inf = 1;
                     }
-                    int64_t first, lastr;
-                    segment_rows(r0, r1 - r0, G::SW, kPersistWarps, seg, &first, &lastr);
-                    if (MODE == D2_SMEM)
-                        pick = warp_rows_find(
-                            first, lastr, [&](int64_t row) { return d2s[row - r0]; }, sbase, t);
-                    else
-                        pick = warp_rows_find(
-                            first, lastr, [&](int64_t row) { return p.d2[row]; }, sbase, t);
+                    if (lane == 0) {
+                        segment_rows(r0, r1 - r0, G::SW, kPersistWarps, seg, &ds.seg_first,
+                                     &ds.seg_last);
+                        ds.seg_before = sbase;
+                        ds.seg_th = t;
+                    }
                 }
-                if (lane == 0) {
-                    p.idx[next] = pick;
-                    st_relaxed_u64(p.mail, ((unsigned long long)pick << 32) |
-                                                 (unsigned long long)(uint32_t)next);
-                    ds.pick = pick;
+                __syncthreads();
+                const int64_t sf = ds.seg_first, sl = ds.seg_last;
+                const int64_t per = 32 * (((sl - sf + 31) / 32 + kPersistWarps - 1) / kPersistWarps);
+                {
+                    const int64_t wb = sf + per * warp;
+                    const int64_t we = (wb + per) < sl ? (wb + per) : sl;
+                    Pair acc{};
+#pragma unroll 4
+                    for (int64_t row = wb + lane; row < we; row += 32)
+                        acc.add(d2_at(row));
+                    const Pair ws = warp_pair_sum(acc);
+                    if (lane == 0)
+                        ds.subsum[warp] = make_float2(ws.hi, ws.lo);
                 }
+                __syncthreads();
+                if (warp == 0) {
+                    Thresh t = ds.seg_th;
+                    const PFind r = warp_pfind(
+                        kPersistWarps, [&](int k) { return Pair{ds.subsum[k].x, ds.subsum[k].y}; },
+                        ds.seg_before, t, false);
+                    Pair wbase = ds.seg_before;
+                    int w;
+                    if (r.index >= 0) {
+                        w = (int)r.index;
+                        wbase = r.before;
+                    } else { // rounding: the last sub-slice with weight
+                        w = r.last_positive >= 0 ? (int)r.last_positive : 0;
+                        t.inf = 1;
+                    }
+                    const int64_t wb = sf + per * w;
+                    const int64_t we = (wb + per) < sl ? (wb + per) : sl;
+                    pick = warp_rows_find(wb < sl ? wb : sf, we, d2_at, wbase, t);
+                }
+            }
+            if (threadIdx.x == 0) {
+                p.idx[next] = pick;
+                st_relaxed_u64(p.mail,
+                               ((unsigned long long)pick << 32) | (unsigned long long)(uint32_t)next);
+                ds.pick = pick;
             }
         } else if (threadIdx.x == 0) {
             ds.pick = wait_mail(p.mail, p.ctl, m, a.timeout_ns);
