@@ -8,9 +8,11 @@ each step is timed with CUDA events on the launching stream.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
                   [--dtype f32|bf16|fp8] [--impl kpp|reference]
 
-Under torchrun (N > 1) every rank seeds its own replica of the workload
-(Philox stream id = rank), with no collective on the data path: weak
-scaling.  Timing is barrier-bracketed and the max over ranks is reported.
+Under torchrun (N > 1), with no collective on the data path: for a single
+problem every rank seeds its own replica of the workload (its own Philox
+stream): weak scaling; for the 512-problem batch the problems are split
+between the ranks: strong scaling.  Timing is barrier-bracketed and the max
+over ranks is reported.
 
 ``--impl reference`` times the FP64 CPU oracle (the correctness reference,
 not a GPU code) on a bounded sample of the same workload on the host cores.
@@ -56,6 +58,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-phi", action="store_true")
     ap.add_argument("--no-sequential", action="store_true")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="skip the autotuner (it runs, untimed, unless a knob is given)")
+    ap.add_argument("--tune-passes", type=int, default=0)
     return ap.parse_args()
 
 
@@ -99,6 +104,28 @@ def profiled_traffic(workload: str, dtype: str):
         return None
     try:
         return int(fields["traffic_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+def profiled_batch_traffic():
+    """DRAM bytes of one step of the batch workload (all waves) from the
+    committed ncu summary, or None if absent or the sources changed since."""
+    path = os.path.join(ROOT, "profiles", f"batched_kernel_{BATCH_WORKLOAD}_f32.md")
+    try:
+        txt = open(path).read()
+    except OSError:
+        return None
+    fields = {}
+    for line in txt.splitlines():
+        if ":" in line and line.split(":", 1)[0] in ("traffic_bytes_per_step",
+                                                     "kernel_source_sha256"):
+            k, v = line.split(":", 1)
+            fields[k] = v.strip()
+    if fields.get("kernel_source_sha256") != kernel_source_hash():
+        return None
+    try:
+        return int(fields["traffic_bytes_per_step"])
     except (KeyError, ValueError):
         return None
 
@@ -220,25 +247,32 @@ def run_reference(args, rank, world):
 
 
 def run_batch(args, rank, world, dev, pg, barrier):
-    """The 512-problem batch: one kpp_seed_batched launch per step, against the
-    same problems seeded one kpp_seed call after another (the plain path)."""
+    """The 512-problem batch: one kpp_seed_batched call per step, against the
+    same problems seeded one kpp_seed call after another (the plain path).
+    With N > 1 ranks the problems are split between the ranks (longest
+    processing time first, no collective on the data path): strong scaling
+    of the fixed 512-problem workload."""
     import ctypes
 
     import numpy as np
     import torch
 
     import paper_1908_02136_gb300 as kpp
-    from paper_1908_02136_gb300 import datagen
+    from paper_1908_02136_gb300 import datagen, multi
 
-    table = datagen.batch_table()
+    full = datagen.batch_table()
+    shards = multi.shard_problems([pr.N * pr.K * pr.d for pr in full], world)
+    table = [full[i] for i in shards[rank]]
     xs = [torch.from_numpy(datagen.batch_problem_points(pr)).to(dev) for pr in table]
     Ks = [pr.K for pr in table]
-    streams = [pr.p + 512 * rank for pr in table]
+    streams = [pr.p for pr in table]
     seeds = [1] * len(table)
     stream = torch.cuda.Stream(dev)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
-    nkd = float(sum(pr.N * pr.K * pr.d for pr in table))
+    nkd_all = float(sum(pr.N * pr.K * pr.d for pr in full))
+    alg_bytes_all = float(sum(pr.N * pr.K * pr.d * 4 for pr in full))
     alg_bytes = float(sum(pr.N * pr.K * pr.d * 4 for pr in table))
+    n_waves = len({pr.d for pr in table})
     with torch.cuda.stream(stream):
         outs, ws = kpp.seed_batched(xs, Ks, seeds, streams, check=True)
         sh = ctypes.c_void_p(stream.cuda_stream)
@@ -305,35 +339,39 @@ def run_batch(args, rank, world, dev, pg, barrier):
             b_.record(stream)
             torch.cuda.synchronize(dev)
             seq_ms = a_.elapsed_time(b_)
-    total_ms = sum(step_ms)
-    if pg is not None:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = multi.max_over_ranks(sum(step_ms), pg, dev)
+    if seq_ms is not None:
+        seq_ms = multi.max_over_ranks(seq_ms, pg, dev)
     ms = total_ms / args.steps
     for (idx, d2, phi), pr in zip(outs, table):
         ih = idx.cpu().numpy()
         assert np.all((ih >= 0) & (ih < pr.N)) and len(set(ih.tolist())) == pr.K
     peaks = measured_peaks()
     peak = peaks["hbm_gbs"] if peaks else 6800.0
+    # the slowest rank's own bytes over its own time would flatter; the
+    # roofline is per GPU: this rank's bytes over the job's step time
     achieved = alg_bytes / (ms / 1e3) / 1e9
+    traffic = profiled_batch_traffic() if world == 1 else None
     if rank == 0:
         print(json.dumps({
-            "metric": METRIC, "value": nkd * world * args.steps / (total_ms / 1e3), "unit": UNIT,
+            "metric": METRIC, "value": nkd_all * args.steps / (total_ms / 1e3), "unit": UNIT,
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": BATCH_WORKLOAD, "problems": len(table), "sum_NKd": nkd,
-                       "form": "batched", "parallelism": f"replicas{world}",
+            "config": {"workload": BATCH_WORKLOAD, "problems": len(full), "sum_NKd": nkd_all,
+                       "problems_on_rank0": len(table), "form": "batched",
+                       "parallelism": f"problems split over {world} ranks (LPT)",
                        "l2": "flushed between steps (512 MiB write)",
                        "plain_sequential_ms": seq_ms,
                        "batched_speedup_vs_plain": (seq_ms / ms) if seq_ms else None},
             "clocks": clocks, "e2e": None,
             # one cooperative launch per distinct d (wave) per step
-            "gpu_launches": args.steps * len({pr.d for pr in table}),
+            "gpu_launches": args.steps * n_waves,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None, "kernel": "batched_kernel",
-                         "algorithmic_bytes_per_launch": alg_bytes},
+                         "frac": achieved / peak, "traffic": traffic,
+                         "kernel": "batched_kernel (all waves of one step)",
+                         "algorithmic_bytes_per_launch": alg_bytes,
+                         "algorithmic_bytes_all_ranks": alg_bytes_all},
             "cpu_baseline": None,
         }), flush=True)
 
@@ -349,7 +387,7 @@ def main():
     import torch
 
     import paper_1908_02136_gb300 as kpp
-    from paper_1908_02136_gb300 import datagen
+    from paper_1908_02136_gb300 import datagen, multi
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
@@ -388,6 +426,19 @@ def main():
     opts.l2_policy = args.l2_policy
     opts.min_rows_per_cta = args.min_rows
     code = {"f32": kpp.F32, "bf16": kpp.BF16, "fp8": kpp.FP8_E4M3}[args.dtype]
+    # the autotuner picks form, lanes per row, row block and cache (untimed);
+    # kpp_seed's automatic choice then uses its winner for this shape
+    knobs = (args.form, args.lanes, args.ctas_per_sm, args.smem_cache, args.alternate,
+             args.l2_policy, args.min_rows)
+    tuned = None
+    if not args.no_tune and not any(knobs):
+        t0 = time.time()
+        try:
+            best, tms = kpp.tune(pts, K, dtype=code, row_scales=scales, passes=args.tune_passes)
+            tuned = {"options": {k: v for k, v in best.items() if v}, "ms_per_pass": tms,
+                     "seconds": round(time.time() - t0, 2)}
+        except kpp.KppError as e:
+            tuned = {"error": str(e)}
     with torch.cuda.device(dev):
         pst, plan = kpp.kpp_describe(N, d, K, code, opts)
     if pst != kpp.OK:
@@ -402,7 +453,7 @@ def main():
     stream = torch.cuda.Stream(dev)
     sh = __import__("ctypes").c_void_p(stream.cuda_stream)
     seed = wl.draw_seed
-    stream_id = rank
+    stream_id = multi.replica_stream(0, rank)
 
     def launch():
         st = kpp.kpp_seed(pts.data_ptr(), None if scales is None else scales.data_ptr(), N, d, K,
@@ -435,11 +486,7 @@ def main():
         clocks = sampler.stop()
         barrier()
     step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
-    total_ms = sum(step_ms)
-    if pg is not None:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = multi.max_over_ranks(sum(step_ms), pg, dev)
     ms_per_step = total_ms / args.steps
     nkd = float(N) * K * d
     value = nkd * world * args.steps / (total_ms / 1e3)
@@ -482,11 +529,7 @@ def main():
                                                       opts=opts, buffers=bufs)
             if st != kpp.OK:
                 raise kpp.KppError(st, "kpp_seed_host")
-        e2e_s = time.perf_counter() - t0
-        if pg is not None:
-            t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
-            pg.all_reduce(t, op=pg.ReduceOp.MAX)
-            e2e_s = float(t.item())
+        e2e_s = multi.max_over_ranks(time.perf_counter() - t0, pg, dev)
         h2d = N * d * eb + (4 * N if scales is not None else 0)
         d2h = 8 * K + 4 * N + 8
         e2e = {"value": nkd * world * e2e_steps / e2e_s, "unit": UNIT,
@@ -535,7 +578,8 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": args.dtype, "data": "synthetic",
             "config": {"workload": wl.name, "N": N, "d": d, "K": K, "storage": args.dtype,
-                       "form": form_name, "plan": plan, "parallelism": f"replicas{world}",
+                       "form": form_name, "plan": plan, "autotuner": tuned,
+                       "parallelism": f"replicas{world}",
                        "l2": "flushed between steps (512 MiB write)",
                        "step_ms_min": min(step_ms), "step_ms_max": max(step_ms)},
             "clocks": clocks, "e2e": e2e, "gpu_launches": launches_per_step * args.steps,

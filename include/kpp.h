@@ -244,6 +244,39 @@ KPP_API kpp_status kpp_seed_batched(const kpp_problem *problems, int32_t n, kpp_
                                     const kpp_options *opts);
 
 /*
+ * Autotuner (not in the paper, which fixes one kernel shape): chooses the
+ * form (persistent or streamed), the lanes that share a point row (how many
+ * points a warp covers per iteration), the smallest row block per CTA, the
+ * CTAs per SM of the streamed grid, the persistent form's shared-memory
+ * point cache, its L2 policy and traversal, by timing the candidates on the
+ * caller's own data: each candidate runs min(K, passes) passes (passes = 0:
+ * min(K, 32)) once untimed and twice timed with CUDA events on `stream`.
+ *   points, row_scales, N, d, K, dtype   as for kpp_seed
+ *   indices_out [K], d2_out [N]          device scratch for the trial runs
+ *                                        (their contents are undefined after)
+ *   workspace   >= kpp_tune_workspace_size(N, d, K, dtype) bytes covers every
+ *               candidate; a smaller one skips the candidates it cannot hold
+ *   best_out    host: the winning options (form never KPP_FORM_AUTO)
+ *   best_ms_per_pass  host, may be NULL: the winner's mean time per pass
+ * Blocks the calling thread (it synchronises `stream`).  The winner is also
+ * recorded per (device, dtype, d, N, K) for the rest of the process: a later
+ * kpp_seed / kpp_workspace_size / kpp_describe for that shape whose options
+ * leave form, lanes_per_row, ctas_per_sm, smem_cache, alternate, l2_policy
+ * and min_rows_per_cta all zero (or opts NULL) uses it (keeping the caller's
+ * timeout_us and use_graph) -- so size the workspace after tuning.
+ * Returns KPP_OK, KPP_ERR_DEGENERATE (the data has fewer than min(K, passes)
+ * distinct points; nothing is recorded), KPP_ERR_UNSUPPORTED (no candidate
+ * could run in the given workspace) or kpp_seed's argument errors.
+ */
+KPP_API size_t kpp_tune_workspace_size(int64_t N, int32_t d, int32_t K, kpp_dtype dtype);
+KPP_API kpp_status kpp_tune(const void *points, const float *row_scales, int64_t N, int32_t d,
+                            int32_t K, kpp_dtype dtype, int64_t *indices_out, float *d2_out,
+                            void *workspace, size_t workspace_bytes, kpp_stream_t stream,
+                            int32_t passes, kpp_options *best_out, float *best_ms_per_pass);
+/* Forgets every shape recorded by kpp_tune in this process. */
+KPP_API void kpp_tune_clear(void);
+
+/*
  * Seeding for callers that cannot allocate device memory.  (The paper has
  * no counterpart; this is a calling convention of this library.)
  *

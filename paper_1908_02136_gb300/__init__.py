@@ -117,6 +117,13 @@ def load_library(build_if_stale: bool = True):
         lib.kpp_read_status.restype = ctypes.c_int
         lib.kpp_quantize.argtypes = [P, I64, I32, ctypes.c_int, P, P, P]
         lib.kpp_quantize.restype = ctypes.c_int
+        lib.kpp_tune_workspace_size.argtypes = [I64, I32, I32, ctypes.c_int]
+        lib.kpp_tune_workspace_size.restype = ctypes.c_size_t
+        lib.kpp_tune.argtypes = [P, P, I64, I32, I32, ctypes.c_int, P, P, P, ctypes.c_size_t, P,
+                                 I32, P, P]
+        lib.kpp_tune.restype = ctypes.c_int
+        lib.kpp_tune_clear.argtypes = []
+        lib.kpp_tune_clear.restype = None
         _lib = lib
         return lib
 
@@ -201,6 +208,24 @@ def kpp_quantize(x, N, d, to, out, row_scales, stream) -> int:
     return load_library().kpp_quantize(x, N, d, to, out, row_scales, stream)
 
 
+def kpp_tune_workspace_size(N, d, K, dtype) -> int:
+    return load_library().kpp_tune_workspace_size(N, d, K, dtype)
+
+
+def kpp_tune(points, row_scales, N, d, K, dtype, indices_out, d2_out, workspace,
+             workspace_bytes, stream, passes, best_out, best_ms_per_pass=None) -> int:
+    """``best_out`` is an ``Options`` (filled); ``best_ms_per_pass`` a ctypes
+    float or None."""
+    ms = None if best_ms_per_pass is None else ctypes.byref(best_ms_per_pass)
+    return load_library().kpp_tune(points, row_scales, N, d, K, dtype, indices_out, d2_out,
+                                   workspace, workspace_bytes, stream, passes,
+                                   ctypes.byref(best_out), ms)
+
+
+def kpp_tune_clear() -> None:
+    load_library().kpp_tune_clear()
+
+
 # ---------------------------------------------------------------------------
 # Tensor helpers.
 # ---------------------------------------------------------------------------
@@ -274,6 +299,32 @@ def seed(points, K: int, seed: int, stream_id: int = 0, *, dtype=None, row_scale
             if st != OK:
                 raise KppError(st, "kpp_seed (device)")
     return idx, d2, phi
+
+
+def tune(points, K: int, *, dtype=None, row_scales=None, passes: int = 0):
+    """Autotune ``kpp_seed`` for this shape on the points' device (``kpp_tune``).
+
+    Returns ``(options dict, ms per pass)``.  The choice is also recorded for
+    later calls with the same shape whose options leave the knobs at zero.
+    """
+    import torch
+
+    N, d = points.shape
+    dt = _dtype_code(points, dtype)
+    dev = points.device
+    idx = torch.empty(K, dtype=torch.int64, device=dev)
+    d2 = torch.empty(N, dtype=torch.float32, device=dev)
+    with torch.cuda.device(dev):
+        n = kpp_tune_workspace_size(N, d, K, dt)
+        ws = torch.empty(max(n, 256), dtype=torch.uint8, device=dev)
+        best = Options()
+        ms = ctypes.c_float(0.0)
+        st = kpp_tune(points.data_ptr(), None if row_scales is None else row_scales.data_ptr(),
+                      N, d, K, dt, idx.data_ptr(), d2.data_ptr(), ws.data_ptr(), ws.numel(),
+                      _stream_handle(dev), passes, best, ms)
+    if st != OK:
+        raise KppError(st, "kpp_tune")
+    return {f: getattr(best, f) for f, _ in Options._fields_ if f != "reserved"}, ms.value
 
 
 def seed_host(points_host, K: int, seed: int, stream_id: int = 0, *, dtype=None,

@@ -200,6 +200,9 @@ kpp_status make_plan(int64_t N, int32_t d, int32_t K, int dt, const kpp_options 
     std::memset(&o, 0, sizeof(o));
     if (opts)
         o = *opts;
+    kpp_options tuned;
+    if (tuned_options(N, d, K, dt, o, &tuned))
+        o = tuned; // the autotuner's choice for this shape
     const int sms = device_sms();
     if (sms <= 0)
         return KPP_ERR_CUDA;

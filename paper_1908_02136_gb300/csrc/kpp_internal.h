@@ -46,6 +46,11 @@ int persistent_segments();
 cudaError_t persistent_launch(const void *fn, int grid, size_t smem, const Problem &p,
                               const PersistArgs &a, cudaStream_t stream);
 
+// The options the autotuner (kpp_tune) recorded for this shape on the
+// current device, if `asked` leaves every knob to the automatic choice.
+bool tuned_options(int64_t N, int32_t d, int32_t K, int dt, const kpp_options &asked,
+                   kpp_options *out);
+
 } // namespace kpp
 
 namespace kpp {

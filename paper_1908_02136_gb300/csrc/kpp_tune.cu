@@ -1,0 +1,234 @@
+// kpp_tune.cu -- the autotuner: chooses the form (persistent or streamed),
+// the lanes per row (points per warp iteration), the row block per CTA and
+// the shared-memory cache by timing the candidates on the caller's own data,
+// and records the winner for the automatic choice of later calls with the
+// same shape.  Host code only; every timed run is an ordinary kpp_seed call.
+#include <algorithm>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
+
+#include "kpp.h"
+#include "kpp_internal.h"
+
+namespace kpp {
+namespace {
+
+struct TuneKey {
+    int dev, dt, d;
+    int64_t N;
+    int32_t K;
+    bool operator<(const TuneKey &o) const
+    {
+        return std::tie(dev, dt, d, N, K) < std::tie(o.dev, o.dt, o.d, o.N, o.K);
+    }
+};
+
+std::mutex g_tune_mutex;
+std::map<TuneKey, kpp_options> g_tuned;
+
+// The knobs the tuner sets are all zero: the caller asked for the automatic
+// choice.
+bool knobs_default(const kpp_options &o)
+{
+    return o.form == KPP_FORM_AUTO && o.lanes_per_row == 0 && o.ctas_per_sm == 0 &&
+           o.smem_cache == 0 && o.alternate == 0 && o.l2_policy == 0 && o.min_rows_per_cta == 0;
+}
+
+kpp_options make_opts(int form, int lanes, int ctas_per_sm, int smem_cache, int min_rows)
+{
+    kpp_options o;
+    std::memset(&o, 0, sizeof(o));
+    o.form = form;
+    o.lanes_per_row = lanes;
+    o.ctas_per_sm = ctas_per_sm;
+    o.smem_cache = smem_cache;
+    o.min_rows_per_cta = min_rows;
+    return o;
+}
+
+// The candidate grid: every built lanes-per-row specialisation of both forms;
+// for the persistent form with and without the shared-memory point cache and
+// three smallest row blocks per CTA, for the streamed form three grid sizes.
+std::vector<kpp_options> candidates()
+{
+    static const int kLanes[] = {0, 1, 2, 4, 8, 16, 32};
+    std::vector<kpp_options> c;
+    for (int lanes : kLanes) {
+        for (int cache : {0, -1})
+            for (int min_rows : {0, 512, 8192})
+                c.push_back(make_opts(KPP_FORM_PERSISTENT, lanes, 0, cache, min_rows));
+        for (int cps : {0, 2, 8})
+            c.push_back(make_opts(KPP_FORM_STREAMED, lanes, cps, 0, 0));
+    }
+    return c;
+}
+
+// What distinguishes two candidates' launches (equal plans run the same code).
+std::tuple<int, int, int, int, int64_t, int64_t, int, int> signature(const kpp_plan &p,
+                                                                   const kpp_options &o)
+{
+    return std::make_tuple(p.form, p.grid, p.lanes_per_row, p.d2_in_smem, p.rows_per_cta,
+                           p.cached_rows_per_cta, o.l2_policy, o.alternate);
+}
+
+} // namespace
+
+bool tuned_options(int64_t N, int32_t d, int32_t K, int dt, const kpp_options &asked,
+                   kpp_options *out)
+{
+    if (!knobs_default(asked))
+        return false;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess)
+        return false;
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    auto it = g_tuned.find(TuneKey{dev, dt, d, N, K});
+    if (it == g_tuned.end())
+        return false;
+    *out = it->second;
+    out->timeout_us = asked.timeout_us; // the caller's bound and graph choice stand
+    out->use_graph = asked.use_graph;
+    return true;
+}
+
+} // namespace kpp
+
+using namespace kpp;
+
+extern "C" {
+
+size_t kpp_tune_workspace_size(int64_t N, int32_t d, int32_t K, kpp_dtype dtype)
+{
+    size_t most = 0;
+    for (const kpp_options &o : candidates()) {
+        kpp_options v = o;
+        for (int l2 : {0, -1, 2}) {
+            v.l2_policy = l2;
+            most = std::max(most, kpp_workspace_size(N, d, K, dtype, &v));
+        }
+    }
+    return most;
+}
+
+void kpp_tune_clear(void)
+{
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    g_tuned.clear();
+}
+
+kpp_status kpp_tune(const void *points, const float *row_scales, int64_t N, int32_t d, int32_t K,
+                    kpp_dtype dtype, int64_t *indices_out, float *d2_out, void *workspace,
+                    size_t workspace_bytes, kpp_stream_t stream, int32_t passes,
+                    kpp_options *best_out, float *best_ms_per_pass)
+{
+    if (!best_out || passes < 0)
+        return KPP_ERR_INVALID_ARG;
+    const int32_t Kt = std::min<int32_t>(K, passes > 0 ? passes : 32);
+    if (Kt < 1)
+        return KPP_ERR_INVALID_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0)
+            cudaEventDestroy(e0);
+        return KPP_ERR_CUDA;
+    }
+    kpp_status result = KPP_OK;
+    float best_ms = -1.f;
+    kpp_options best;
+    std::memset(&best, 0, sizeof(best));
+    std::vector<std::tuple<int, int, int, int, int64_t, int64_t, int, int>> seen;
+
+    // one candidate: a warm-up run (it also captures a streamed graph), then
+    // two timed runs; ms per pass, or < 0 if the candidate does not apply
+    auto trial = [&](const kpp_options &o, float *ms) -> kpp_status {
+        *ms = -1.f;
+        kpp_plan plan;
+        if (kpp_describe(N, d, Kt, dtype, &o, &plan) != KPP_OK ||
+            (size_t)plan.workspace_bytes > workspace_bytes)
+            return KPP_OK;
+        const auto sig = signature(plan, o);
+        if (std::find(seen.begin(), seen.end(), sig) != seen.end())
+            return KPP_OK;
+        seen.push_back(sig);
+        kpp_status st = kpp_seed(points, row_scales, N, d, Kt, dtype, 1, 0, nullptr, 0,
+                                 indices_out, d2_out, nullptr, workspace, workspace_bytes, stream,
+                                 &o);
+        if (st != KPP_OK)
+            return st == KPP_ERR_INVALID_ARG || st == KPP_ERR_WORKSPACE ? st : KPP_OK;
+        st = kpp_read_status(workspace, stream);
+        if (st == KPP_ERR_DEGENERATE || st == KPP_ERR_CUDA)
+            return st; // the data or the device, not the candidate
+        if (st != KPP_OK)
+            return KPP_OK; // e.g. a bounded wait gave up: not a candidate
+        constexpr int kRuns = 2;
+        if (cudaEventRecord(e0, s) != cudaSuccess)
+            return KPP_ERR_CUDA;
+        for (int r = 0; r < kRuns; ++r) {
+            st = kpp_seed(points, row_scales, N, d, Kt, dtype, 1, 0, nullptr, 0, indices_out,
+                          d2_out, nullptr, workspace, workspace_bytes, stream, &o);
+            if (st != KPP_OK)
+                return KPP_OK;
+        }
+        float t = 0.f;
+        if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+            cudaEventElapsedTime(&t, e0, e1) != cudaSuccess)
+            return KPP_ERR_CUDA;
+        if (kpp_read_status(workspace, stream) != KPP_OK)
+            return KPP_OK;
+        *ms = t / (kRuns * Kt);
+        return KPP_OK;
+    };
+    auto consider = [&](const kpp_options &o) -> kpp_status {
+        float ms;
+        const kpp_status st = trial(o, &ms);
+        if (st == KPP_OK && ms > 0.f && (best_ms < 0.f || ms < best_ms)) {
+            best_ms = ms;
+            best = o;
+        }
+        return st;
+    };
+
+    for (const kpp_options &o : candidates()) {
+        result = consider(o);
+        if (result != KPP_OK)
+            break;
+    }
+    // refine the persistent winner's traversal and L2 policy
+    if (result == KPP_OK && best_ms > 0.f && best.form == KPP_FORM_PERSISTENT) {
+        const kpp_options base = best;
+        for (int l2 : {-1, 2}) {
+            kpp_options v = base;
+            v.l2_policy = l2;
+            if ((result = consider(v)) != KPP_OK)
+                break;
+        }
+        if (result == KPP_OK) {
+            kpp_options v = best;
+            v.alternate = -1;
+            result = consider(v);
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (result != KPP_OK)
+        return result;
+    if (best_ms < 0.f)
+        return KPP_ERR_UNSUPPORTED; // no candidate ran (workspace too small?)
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess)
+        return KPP_ERR_CUDA;
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        g_tuned[TuneKey{dev, (int)dtype, d, N, K}] = best;
+    }
+    *best_out = best;
+    if (best_ms_per_pass)
+        *best_ms_per_pass = best_ms;
+    return KPP_OK;
+}
+
+} // extern "C"

@@ -30,7 +30,8 @@ def test_header_declares_the_boundary():
     names = declared_entry_points()
     for required in ["kpp_seed", "kpp_workspace_size", "kpp_read_status", "kpp_quantize",
                      "kpp_seed_host", "kpp_status_string", "kpp_version", "kpp_describe",
-                     "kpp_seed_batched", "kpp_batch_workspace_size", "kpp_seed_noalloc"]:
+                     "kpp_seed_batched", "kpp_batch_workspace_size", "kpp_seed_noalloc",
+                     "kpp_tune", "kpp_tune_workspace_size", "kpp_tune_clear"]:
         assert required in names
 
 
@@ -56,6 +57,7 @@ def test_host_only_entry_points(lib):
         s = kpp.kpp_status_string(code)
         assert isinstance(s, str) and s and s != "unknown status"
     assert kpp.kpp_status_string(99) == "unknown status"
+    kpp.kpp_tune_clear()  # host-side table only
 
 
 def test_invalid_arguments_fail_synchronously(lib):
