@@ -61,6 +61,9 @@ def parse():
     ap.add_argument("--no-tune", action="store_true",
                     help="skip the autotuner (it runs, untimed, unless a knob is given)")
     ap.add_argument("--tune-passes", type=int, default=0)
+    ap.add_argument("--n-points", type=int, default=0,
+                    help="a smaller instance of the workload's recipe (profiling)")
+    ap.add_argument("--k-seeds", type=int, default=0)
     return ap.parse_args()
 
 
@@ -71,14 +74,26 @@ def dist_env():
     return rank, world, local
 
 
-def kernel_source_hash():
-    """SHA-256 over the CUDA sources and the C header (to tell whether a
-    committed ncu traffic figure still describes the kernel being run)."""
-    import glob
+# The sources each kernel is compiled from (device code and the host code
+# that plans and launches it): an ncu figure stays valid while these are
+# unchanged.
+KERNEL_SOURCES = {
+    "persistent": ["kpp_device.cuh", "kpp_pass.cuh", "kpp_persistent.cuh", "kpp_persistent.cu",
+                   "kpp_persistent_f32.cu", "kpp_persistent_bf16.cu", "kpp_persistent_fp8.cu"],
+    "streamed": ["kpp_device.cuh", "kpp_pass.cuh", "kpp_streamed.cu"],
+    "batched": ["kpp_device.cuh", "kpp_pass.cuh", "kpp_persistent.cuh", "kpp_batched.cuh",
+                "kpp_batched.cu", "kpp_batched_f32.cu", "kpp_batched_bf16.cu",
+                "kpp_batched_fp8.cu"],
+}
+
+
+def kernel_source_hash(kind: str = "persistent"):
+    """SHA-256 over one kernel's CUDA sources and the C header (to tell whether
+    a committed ncu traffic figure still describes the kernel being run)."""
     import hashlib
 
     h = hashlib.sha256()
-    files = sorted(glob.glob(os.path.join(ROOT, "paper_1908_02136_gb300", "csrc", "*")))
+    files = [os.path.join(ROOT, "paper_1908_02136_gb300", "csrc", f) for f in KERNEL_SOURCES[kind]]
     files.append(os.path.join(ROOT, "include", "kpp.h"))
     for f in files:
         h.update(os.path.basename(f).encode())
@@ -86,24 +101,38 @@ def kernel_source_hash():
     return h.hexdigest()
 
 
-def profiled_traffic(workload: str, dtype: str):
-    """DRAM bytes per launch from the committed ncu summary of this workload,
-    or None if there is none or the kernel sources changed since."""
-    path = os.path.join(ROOT, "profiles", f"persistent_kernel_{workload}_{dtype}.md")
+def plan_signature(plan: dict) -> str:
+    """The launch shape an ncu figure was taken with."""
+    keys = ("form", "grid", "lanes_per_row", "d2_in_smem", "rows_per_cta", "cached_rows_per_cta")
+    return " ".join(f"{k}={plan[k]}" for k in keys)
+
+
+def _profile_fields(path: str, names) -> dict:
     try:
         txt = open(path).read()
     except OSError:
-        return None
+        return {}
     fields = {}
     for line in txt.splitlines():
-        if ":" in line and line.split(":", 1)[0] in ("traffic_bytes_per_launch",
-                                                     "kernel_source_sha256"):
+        if ":" in line and line.split(":", 1)[0] in names:
             k, v = line.split(":", 1)
             fields[k] = v.strip()
-    if fields.get("kernel_source_sha256") != kernel_source_hash():
+    return fields
+
+
+def profiled_traffic(kind: str, workload: str, dtype: str, plan: dict):
+    """DRAM bytes per launch from the committed ncu summary of this kernel on
+    this workload, or None if there is none, its launch shape differs or its
+    sources changed since."""
+    path = os.path.join(ROOT, "profiles", f"{kind}_kernel_{workload}_{dtype}.md")
+    f = _profile_fields(path, ("traffic_bytes_per_launch", "kernel_source_sha256",
+                               "plan_signature"))
+    if f.get("kernel_source_sha256") != kernel_source_hash(kind):
+        return None
+    if f.get("plan_signature") != plan_signature(plan):
         return None
     try:
-        return int(fields["traffic_bytes_per_launch"])
+        return int(f["traffic_bytes_per_launch"])
     except (KeyError, ValueError):
         return None
 
@@ -112,20 +141,11 @@ def profiled_batch_traffic():
     """DRAM bytes of one step of the batch workload (all waves) from the
     committed ncu summary, or None if absent or the sources changed since."""
     path = os.path.join(ROOT, "profiles", f"batched_kernel_{BATCH_WORKLOAD}_f32.md")
-    try:
-        txt = open(path).read()
-    except OSError:
-        return None
-    fields = {}
-    for line in txt.splitlines():
-        if ":" in line and line.split(":", 1)[0] in ("traffic_bytes_per_step",
-                                                     "kernel_source_sha256"):
-            k, v = line.split(":", 1)
-            fields[k] = v.strip()
-    if fields.get("kernel_source_sha256") != kernel_source_hash():
+    f = _profile_fields(path, ("traffic_bytes_per_step", "kernel_source_sha256"))
+    if f.get("kernel_source_sha256") != kernel_source_hash("batched"):
         return None
     try:
-        return int(fields["traffic_bytes_per_step"])
+        return int(f["traffic_bytes_per_step"])
     except (KeyError, ValueError):
         return None
 
@@ -406,6 +426,11 @@ def main():
         run_batch(args, rank, world, dev, pg, barrier)
         return
     wl = datagen.WORKLOADS[args.workload]
+    if args.n_points or args.k_seeds:
+        import dataclasses
+
+        n_, k_ = args.n_points or wl.N, args.k_seeds or wl.K
+        wl = dataclasses.replace(wl, N=n_, K=k_, name=f"{wl.name}@N{n_}K{k_}")
     x_np = datagen.workload_points(wl) if wl.N <= 2_000_000 else None
     x = torch.from_numpy(x_np).to(dev) if x_np is not None else datagen.workload_points(wl, dev)
     N, d, K = wl.N, wl.d, wl.K
@@ -547,7 +572,7 @@ def main():
     d2_bytes = 8 * N if form_name == "streamed" else 0  # D^2 stays on chip when persistent
     alg_bytes = passes_per_launch * (point_bytes + d2_bytes)
     achieved = alg_bytes / (per_launch_ms / 1e3) / 1e9
-    traffic = profiled_traffic(wl.name, args.dtype) if form_name == "persistent" else None
+    traffic = profiled_traffic(form_name, wl.name, args.dtype, plan)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic,
                 "peak_source": "measured" if peaks else "fallback",

@@ -250,7 +250,9 @@ KPP_API kpp_status kpp_seed_batched(const kpp_problem *problems, int32_t n, kpp_
  * CTAs per SM of the streamed grid, the persistent form's shared-memory
  * point cache, its L2 policy and traversal, by timing the candidates on the
  * caller's own data: each candidate runs min(K, passes) passes (passes = 0:
- * min(K, 32)) once untimed and twice timed with CUDA events on `stream`.
+ * min(K, 32)) once untimed and twice timed with CUDA events on `stream`;
+ * candidates are tried defaults first, and a later one replaces the best so
+ * far only if it is more than 1 % faster.
  *   points, row_scales, N, d, K, dtype   as for kpp_seed
  *   indices_out [K], d2_out [N]          device scratch for the trial runs
  *                                        (their contents are undefined after)

@@ -185,7 +185,9 @@ kpp_status kpp_tune(const void *points, const float *row_scales, int64_t N, int3
     auto consider = [&](const kpp_options &o) -> kpp_status {
         float ms;
         const kpp_status st = trial(o, &ms);
-        if (st == KPP_OK && ms > 0.f && (best_ms < 0.f || ms < best_ms)) {
+        // a later candidate must win by more than 1 %: timing noise alone
+        // does not move the choice away from the earlier (default) ones
+        if (st == KPP_OK && ms > 0.f && (best_ms < 0.f || ms < 0.99f * best_ms)) {
             best_ms = ms;
             best = o;
         }
