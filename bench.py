@@ -61,6 +61,8 @@ def parse():
     ap.add_argument("--no-tune", action="store_true",
                     help="skip the autotuner (it runs, untimed, unless a knob is given)")
     ap.add_argument("--tune-passes", type=int, default=0)
+    ap.add_argument("--phi-seeds", type=int, default=0,
+                    help="precision forms: also compare mean phi over this many draw seeds")
     ap.add_argument("--n-points", type=int, default=0,
                     help="a smaller instance of the workload's recipe (profiling)")
     ap.add_argument("--k-seeds", type=int, default=0)
@@ -396,6 +398,37 @@ def run_batch(args, rank, world, dev, pg, barrier):
         }), flush=True)
 
 
+def phi_over_seeds(kpp, x, pts, scales, code, K, seed0, stream_id, R, stream, dev):
+    """Mean seeding cost over R draw seeds, precision form vs FP32: the form's
+    seeds scored on the original FP32 points (replayed through the FP32 path)
+    against FP32 seeding with the same draw seeds; means with 95 % intervals
+    and the paired relative difference."""
+    import torch
+
+    form, fp32 = [], []
+    with torch.cuda.stream(stream):
+        for r in range(R):
+            sd = seed0 + 1000 + r
+            idx, _, _ = kpp.seed(pts, K, sd, stream_id, dtype=code, row_scales=scales, check=True)
+            _, _, p_form = kpp.seed(x, K, sd, stream_id, forced=idx.clone(), check=True)
+            _, _, p32 = kpp.seed(x, K, sd, stream_id, check=True)
+            form.append(float(p_form.item()))
+            fp32.append(float(p32.item()))
+    torch.cuda.synchronize(dev)
+
+    def summary(v):
+        m = statistics.fmean(v)
+        half = 1.96 * statistics.stdev(v) / math.sqrt(len(v))
+        return {"mean": m, "ci95": half}
+
+    rel = [(a - b) / b for a, b in zip(form, fp32)]
+    sf, s32, sr = summary(form), summary(fp32), summary(rel)
+    return {"seeds": R, "phi_form_on_fp32_points": sf, "phi_fp32": s32,
+            "rel_diff_of_means": (sf["mean"] - s32["mean"]) / s32["mean"],
+            "paired_rel_diff": sr,
+            "means_agree_within_ci": abs(sf["mean"] - s32["mean"]) <= sf["ci95"] + s32["ci95"]}
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -535,6 +568,9 @@ def main():
                      "phi_rel_diff": abs(phi_form - phi_orig) / phi_orig,
                      "phi_fp32_same_seed": phi32,
                      "phi_vs_fp32_run": (phi_orig - phi32) / phi32}
+        if args.phi_seeds > 1:
+            precision["over_seeds"] = phi_over_seeds(kpp, x, pts, scales, code, K, wl.draw_seed,
+                                                     stream_id, args.phi_seeds, stream, dev)
 
     # e2e: host points (pinned) -> C ABI -> host results, wall clock incl. copies
     e2e = None

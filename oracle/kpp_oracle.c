@@ -19,7 +19,7 @@
  *     centre coordinates are looked up from the point array by that index.
  *   - Section II (Thrust reduction): the sum of all D^2 is taken in double.
  *
- * Readings where the paper is silent (each is repeated in the design doc):
+ * Readings where the paper is silent (the CUDA library implements the same):
  *   R1  The random draw is u_m = Philox4x64-10(key = {seed, stream},
  *       counter = {m, 0, 0, 0}), word 0 mapped to [0,1) as (w0 >> 11) * 2^-53.
  *       Philox4x64-10 follows Salmon, Moraes, Dror and Shaw, "Parallel Random
