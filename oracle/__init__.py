@@ -4,6 +4,8 @@ TEST INFRASTRUCTURE ONLY: the correctness reference the CUDA library is
 checked against.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
 ``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import it.
 It shares no code with ``paper_1908_02136_gb300`` and never calls it.
+Besides the seeding it holds one Lloyd iteration (readings L1-L3), the
+clustering stage the seeds are for.
 
 The arithmetic lives in ``kpp_oracle.c`` (plain C, serial, FP64, built with
 ``gcc -O2 -ffp-contract=off``); this module only compiles it and marshals
@@ -94,6 +96,9 @@ def _load():
             P, P, ctypes.c_int, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
             ctypes.c_uint64, ctypes.c_uint64, P, ctypes.c_int32, P, P, P, P, P]
         lib.kpp_oracle_seed.restype = ctypes.c_int
+        lib.kpp_oracle_lloyd_step.argtypes = [
+            P, P, ctypes.c_int, ctypes.c_int64, ctypes.c_int32, P, ctypes.c_int32, P, P, P, P, P]
+        lib.kpp_oracle_lloyd_step.restype = ctypes.c_int
         _lib = lib
         return lib
 
@@ -210,3 +215,32 @@ def seed(points: np.ndarray, K: int, seed: int, stream: int = 0, *, dtype=None,
     if history:
         out["d2_hist"] = hist
     return out
+
+
+def lloyd_step(points: np.ndarray, centres: np.ndarray, *, dtype=None,
+               scales: np.ndarray | None = None) -> dict:
+    """One FP64 Lloyd iteration (readings L1-L3): assignment to the nearest
+    centre, then each centre moved to the mean of its points.
+
+    ``points`` stored values [N, d] (float32, BF16 bits as uint16, or E4M3
+    codes as uint8 with ``scales``); ``centres`` [K, d] (cast to float64).
+    Returns labels (int32), d2, centres (float64), counts (int64), phi.
+    """
+    pts = np.ascontiguousarray(points)
+    N, d = pts.shape
+    code = _dtype_code(pts, dtype)
+    C = np.ascontiguousarray(centres, dtype=np.float64)
+    K = C.shape[0]
+    if C.shape[1] != d:
+        raise ValueError("centres must have the points' dimension")
+    sc = None if scales is None else np.ascontiguousarray(scales, dtype=np.float32)
+    labels = np.empty(N, dtype=np.int32)
+    d2 = np.empty(N, dtype=np.float64)
+    out = np.empty((K, d), dtype=np.float64)
+    counts = np.empty(K, dtype=np.int64)
+    phi = ctypes.c_double()
+    st = _load().kpp_oracle_lloyd_step(_ptr(pts), _ptr(sc), code, N, d, _ptr(C), K, _ptr(labels),
+                                       _ptr(d2), _ptr(out), _ptr(counts), ctypes.byref(phi))
+    if st != OK:
+        raise ValueError(f"kpp_oracle_lloyd_step: status {st}")
+    return {"labels": labels, "d2": d2, "centres": out, "counts": counts, "phi": phi.value}

@@ -50,6 +50,16 @@
  *         all-zero row), q_ij = RNE-with-saturation of the FP32 quotient
  *         x_ij / s_i.
  *
+ * Lloyd iteration (the clustering stage after seeding; Section II says it is
+ * implemented as the standard K-means algorithm, i.e. Lloyd's):
+ *   L1  Assignment: label_i = argmin_k sum_j (x_ij - c_kj)^2 in FP64, the
+ *       difference form summed over j in order; the smallest k wins a tie.
+ *   L2  Update: c'_k = (sum of the points labelled k, FP64, index order) /
+ *       count_k; a centre that no point chose keeps its position (the paper
+ *       is silent on empty clusters).
+ *   L3  phi = sum_i of the assigned squared distances (FP64, index order),
+ *       the cost of the assignment, before the update.
+ *
  * Build: gcc -O2 -ffp-contract=off -shared -fPIC (no fused multiply-add, so
  * the arithmetic is the one written here on every host).
  */
@@ -375,4 +385,75 @@ int kpp_oracle_seed(const void *points, const float *scales, int dtype, int64_t 
     }
     free(X);
     return status;
+}
+
+/* ------------------------------------------------------------------------ */
+/* One Lloyd iteration (readings L1-L3).                                      */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * points [N x d] stored values (decoded as in R5), centres [K x d] FP64.
+ * Outputs: labels [N], d2 [N] (squared distance to the assigned centre),
+ * centres_out [K x d], counts [K], phi.  Any output may be NULL except
+ * labels.  Returns KPP_ORACLE_OK or KPP_ORACLE_INVALID.
+ */
+int kpp_oracle_lloyd_step(const void *points, const float *scales, int dtype, int64_t N,
+                          int32_t d, const double *centres, int32_t K, int32_t *labels,
+                          double *d2, double *centres_out, int64_t *counts, double *phi)
+{
+    if (!points || !centres || !labels || N < 1 || d < 1 || K < 1)
+        return KPP_ORACLE_INVALID;
+    if (dtype == KPP_ORACLE_FP8_E4M3 && !scales)
+        return KPP_ORACLE_INVALID;
+    double *x = (double *)malloc(sizeof(double) * (size_t)d);
+    double *sum = (double *)calloc((size_t)K * (size_t)d, sizeof(double));
+    int64_t *cnt = (int64_t *)calloc((size_t)K, sizeof(int64_t));
+    if (!x || !sum || !cnt) {
+        free(x);
+        free(sum);
+        free(cnt);
+        return KPP_ORACLE_INVALID;
+    }
+    double total = 0.0;
+    for (int64_t i = 0; i < N; ++i) {
+        for (int32_t j = 0; j < d; ++j)
+            x[j] = coord(points, scales, dtype, i, d, j);
+        int32_t best = 0;
+        double best_d = INFINITY;
+        for (int32_t k = 0; k < K; ++k) {
+            const double *c = centres + (int64_t)k * d;
+            double s = 0.0;
+            for (int32_t j = 0; j < d; ++j) {
+                double t = x[j] - c[j];
+                s += t * t;
+            }
+            if (s < best_d) { /* strict: the smallest k wins a tie (L1) */
+                best_d = s;
+                best = k;
+            }
+        }
+        labels[i] = best;
+        if (d2)
+            d2[i] = best_d;
+        total += best_d;
+        cnt[best] += 1;
+        double *acc = sum + (int64_t)best * d;
+        for (int32_t j = 0; j < d; ++j)
+            acc[j] += x[j];
+    }
+    if (centres_out) {
+        for (int32_t k = 0; k < K; ++k)
+            for (int32_t j = 0; j < d; ++j)
+                centres_out[(int64_t)k * d + j] =
+                    cnt[k] > 0 ? sum[(int64_t)k * d + j] / (double)cnt[k]
+                               : centres[(int64_t)k * d + j]; /* L2: empty keeps */
+    }
+    if (counts)
+        memcpy(counts, cnt, sizeof(int64_t) * (size_t)K);
+    if (phi)
+        *phi = total;
+    free(x);
+    free(sum);
+    free(cnt);
+    return KPP_ORACLE_OK;
 }
