@@ -37,6 +37,7 @@ METRIC = "k-means++ seeding ms & N·K·d/s; HBM GB/s vs peak; BF16/batched vs FP
 UNIT = "N*K*d/s"
 DEFAULT_WORKLOAD = "gmm-N1e6-d32-K256"
 BATCH_WORKLOAD = "batch-512"
+LLOYD_PREFIX = "lloyd-"  # e.g. lloyd-gmm-N1e7-d64-K1024: one Lloyd iteration from the seeds
 
 
 def parse():
@@ -429,6 +430,124 @@ def phi_over_seeds(kpp, x, pts, scales, code, K, seed0, stream_id, R, stream, de
             "means_agree_within_ci": abs(sf["mean"] - s32["mean"]) <= sf["ci95"] + s32["ci95"]}
 
 
+def run_lloyd(args, rank, world, dev, pg, barrier):
+    """One Lloyd iteration (assignment on the tensor cores + update) on a
+    seeding workload's points, from that workload's k-means++ seeds: each
+    step is kpp_lloyd_step from the same seeds; the assignment alone is also
+    timed (kpp_lloyd_assign) for its tensor roofline."""
+    import ctypes
+
+    import numpy as np
+    import torch
+
+    import paper_1908_02136_gb300 as kpp
+    from paper_1908_02136_gb300 import datagen, multi
+
+    wl = datagen.WORKLOADS[args.workload[len(LLOYD_PREFIX):]]
+    x = datagen.workload_points(wl, dev)
+    N, d, K = wl.N, wl.d, wl.K
+    stream = torch.cuda.Stream(dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    with torch.cuda.stream(stream):
+        idx, _, _ = kpp.seed(x, K, wl.draw_seed, multi.replica_stream(0, rank))
+        C = x[idx].contiguous()
+        ll = kpp.Lloyd(x, K)
+        labels = torch.empty(N, dtype=torch.int32, device=dev)
+        d2 = torch.empty(N, dtype=torch.float32, device=dev)
+        C2 = torch.empty_like(C)
+        counts = torch.empty(K, dtype=torch.int64, device=dev)
+        phi = torch.empty(1, dtype=torch.float64, device=dev)
+        sh = ctypes.c_void_p(stream.cuda_stream)
+
+        def step():
+            st = kpp.kpp_lloyd_step(x.data_ptr(), N, d, C.data_ptr(), K, labels.data_ptr(),
+                                    d2.data_ptr(), C2.data_ptr(), counts.data_ptr(),
+                                    phi.data_ptr(), ll.ws.data_ptr(), ll.ws.numel(), sh)
+            if st != kpp.OK:
+                raise kpp.KppError(st, "kpp_lloyd_step")
+
+        def assign():
+            st = kpp.kpp_lloyd_assign(C.data_ptr(), N, d, K, labels.data_ptr(), ll.ws.data_ptr(),
+                                      ll.ws.numel(), sh)
+            if st != kpp.OK:
+                raise kpp.KppError(st, "kpp_lloyd_assign")
+
+        def timed(fn, steps):
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                  for _ in range(steps)]
+            for a_, b_ in ev:
+                flush.fill_(3)
+                a_.record(stream)
+                fn()
+                b_.record(stream)
+            torch.cuda.synchronize(dev)
+            return [a_.elapsed_time(b_) for a_, b_ in ev]
+
+        for _ in range(args.warmup):
+            flush.fill_(1)
+            step()
+        st = kpp.kpp_read_status(ll.ws.data_ptr(), sh)
+        if st != kpp.OK:
+            raise kpp.KppError(st, "warmup")
+        torch.cuda.synchronize(dev)
+        barrier()
+        sampler = ClockSampler(int(str(dev).split(":")[-1]) if ":" in str(dev) else 0)
+        sampler.start()
+        time.sleep(0.3)
+        step_ms = timed(step, args.steps)
+        assign_ms = timed(assign, args.steps)
+        clocks = sampler.stop()
+        barrier()
+        st = kpp.kpp_read_status(ll.ws.data_ptr(), sh)
+        if st != kpp.OK:
+            raise kpp.KppError(st, "timed steps")
+    total_ms = multi.max_over_ranks(sum(step_ms), pg, dev)
+    ms = total_ms / args.steps
+    a_ms = statistics.fmean(assign_ms)
+    nkd = float(N) * K * d
+    dp = 64 if d <= 64 else 128
+    kpad = (K + 127) // 128 * 128
+    tensor_flops = 3 * 2.0 * N * kpad * dp  # hi.hi + hi.lo + lo.hi, padded tiles
+    peaks = measured_peaks()
+    peak = peaks["bf16_tflops"] if peaks else 1900.0
+    achieved = tensor_flops / (a_ms / 1e3) / 1e12
+    # bounded CPU sample: the oracle's Lloyd step on the first points
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+
+        n_s = max(1, min(N, int(3e9 / (K * d))))
+        xs = x[:n_s].cpu().numpy()
+        t0 = time.perf_counter()
+        oracle.lloyd_step(xs, C.double().cpu().numpy())
+        dt = time.perf_counter() - t0
+        cores, model = cpu_info()
+        cpu = {"value": n_s * K * d / dt, "unit": "N*K*d/s", "cores": 1, "kind": "oracle",
+               "sample": f"{n_s} of {N} points, all {K} centres, one Lloyd step (serial FP64)",
+               "host_cores": cores, "cpu": model}
+    if rank == 0:
+        print(json.dumps({
+            "metric": "k-means Lloyd iteration N*K*d/s (after k-means++ seeding)",
+            "value": nkd * world * args.steps / (total_ms / 1e3), "unit": "N*K*d/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "N": N, "d": d, "K": K,
+                       "assignment": "tcgen05 BF16 split (hi.hi + hi.lo + lo.hi), FP32 accumulate",
+                       "assign_ms": a_ms, "parallelism": f"replicas{world}",
+                       "l2": "flushed between steps (512 MiB write)",
+                       "phi": float(phi.item())},
+            "clocks": clocks, "e2e": None, "gpu_launches": 5 * args.steps,
+            "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak,
+                         "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                         "kernel": "lloyd_assign_kernel",
+                         "tensor_flops_per_launch": tensor_flops,
+                         "algorithmic_flops_per_launch": 2.0 * nkd,
+                         "peak_source": "measured bf16 (burst)" if peaks else "fallback"},
+            "cpu_baseline": cpu,
+        }), flush=True)
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -457,6 +576,9 @@ def main():
 
     if args.workload == BATCH_WORKLOAD:
         run_batch(args, rank, world, dev, pg, barrier)
+        return
+    if args.workload.startswith(LLOYD_PREFIX):
+        run_lloyd(args, rank, world, dev, pg, barrier)
         return
     wl = datagen.WORKLOADS[args.workload]
     if args.n_points or args.k_seeds:

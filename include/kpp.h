@@ -279,6 +279,48 @@ KPP_API kpp_status kpp_tune(const void *points, const float *row_scales, int64_t
 KPP_API void kpp_tune_clear(void);
 
 /*
+ * One Lloyd iteration -- the clustering stage the seeds are for (Section II:
+ * "the clustering part is implemented the same as the K-means algorithm"):
+ * every point is assigned to its nearest centre (squared Euclidean; the
+ * smallest index wins a tie), then every centre moves to the mean of its
+ * points; a centre no point chose keeps its position.
+ *   points      [N x d] FP32 device, d <= 128, 1 <= K <= min(N, 4096)
+ *   centres     [K x d] FP32 device (e.g. the seeded points)
+ *   labels_out  [N] int32: the assigned centre
+ *   d2_out      [N] FP32 or NULL: squared distance to it (FP32 difference
+ *               form, the seeding pass's arithmetic)
+ *   centres_out [K x d] FP32: the means (may not alias `centres`)
+ *   counts_out  [K] int64 or NULL: points per centre
+ *   phi_out     [1] FP64 or NULL: sum of d2 (the cost of the assignment)
+ *   workspace   >= kpp_lloyd_workspace_size(N, d, K) bytes, 256-byte aligned,
+ *               prepared once by kpp_lloyd_prepare for these points
+ * The assignment runs on the tensor cores: |c|^2 - 2 x.c with x and c split
+ * into two BF16 planes (hi + lo) and x.c = hi.hi + hi.lo + lo.hi accumulated
+ * in FP32, so a label can differ from the exact nearest centre only when two
+ * centres are within ~2^-15 |x||c| of each other.  kpp_lloyd_prepare writes
+ * the split of the points into the workspace; call it again whenever the
+ * points change.  Asynchronous on `stream`; a bounded wait that gave up is
+ * reported as KPP_ERR_TIMEOUT by kpp_read_status(workspace).
+ */
+KPP_API size_t kpp_lloyd_workspace_size(int64_t N, int32_t d, int32_t K);
+KPP_API kpp_status kpp_lloyd_prepare(const float *points, int64_t N, int32_t d, int32_t K,
+                                     void *workspace, size_t workspace_bytes,
+                                     kpp_stream_t stream);
+/*
+ * The assignment half alone: labels_out [N] int32 = nearest of the K
+ * centres [K x d] FP32 for the points prepared in `workspace` (same rule and
+ * bound as kpp_lloyd_step).
+ */
+KPP_API kpp_status kpp_lloyd_assign(const float *centres, int64_t N, int32_t d, int32_t K,
+                                    int32_t *labels_out, void *workspace,
+                                    size_t workspace_bytes, kpp_stream_t stream);
+KPP_API kpp_status kpp_lloyd_step(const float *points, int64_t N, int32_t d,
+                                  const float *centres, int32_t K, int32_t *labels_out,
+                                  float *d2_out, float *centres_out, int64_t *counts_out,
+                                  double *phi_out, void *workspace, size_t workspace_bytes,
+                                  kpp_stream_t stream);
+
+/*
  * Seeding for callers that cannot allocate device memory.  (The paper has
  * no counterpart; this is a calling convention of this library.)
  *

@@ -124,6 +124,14 @@ def load_library(build_if_stale: bool = True):
         lib.kpp_tune.restype = ctypes.c_int
         lib.kpp_tune_clear.argtypes = []
         lib.kpp_tune_clear.restype = None
+        lib.kpp_lloyd_workspace_size.argtypes = [I64, I32, I32]
+        lib.kpp_lloyd_workspace_size.restype = ctypes.c_size_t
+        lib.kpp_lloyd_prepare.argtypes = [P, I64, I32, I32, P, ctypes.c_size_t, P]
+        lib.kpp_lloyd_prepare.restype = ctypes.c_int
+        lib.kpp_lloyd_step.argtypes = [P, I64, I32, P, I32, P, P, P, P, P, P, ctypes.c_size_t, P]
+        lib.kpp_lloyd_step.restype = ctypes.c_int
+        lib.kpp_lloyd_assign.argtypes = [P, I64, I32, I32, P, P, ctypes.c_size_t, P]
+        lib.kpp_lloyd_assign.restype = ctypes.c_int
         _lib = lib
         return lib
 
@@ -226,6 +234,26 @@ def kpp_tune_clear() -> None:
     load_library().kpp_tune_clear()
 
 
+def kpp_lloyd_workspace_size(N, d, K) -> int:
+    return load_library().kpp_lloyd_workspace_size(N, d, K)
+
+
+def kpp_lloyd_prepare(points, N, d, K, workspace, workspace_bytes, stream) -> int:
+    return load_library().kpp_lloyd_prepare(points, N, d, K, workspace, workspace_bytes, stream)
+
+
+def kpp_lloyd_assign(centres, N, d, K, labels_out, workspace, workspace_bytes, stream) -> int:
+    return load_library().kpp_lloyd_assign(centres, N, d, K, labels_out, workspace,
+                                           workspace_bytes, stream)
+
+
+def kpp_lloyd_step(points, N, d, centres, K, labels_out, d2_out, centres_out, counts_out, phi_out,
+                   workspace, workspace_bytes, stream) -> int:
+    return load_library().kpp_lloyd_step(points, N, d, centres, K, labels_out, d2_out,
+                                         centres_out, counts_out, phi_out, workspace,
+                                         workspace_bytes, stream)
+
+
 # ---------------------------------------------------------------------------
 # Tensor helpers.
 # ---------------------------------------------------------------------------
@@ -325,6 +353,73 @@ def tune(points, K: int, *, dtype=None, row_scales=None, passes: int = 0):
     if st != OK:
         raise KppError(st, "kpp_tune")
     return {f: getattr(best, f) for f, _ in Options._fields_ if f != "reserved"}, ms.value
+
+
+class Lloyd:
+    """Lloyd iterations on FP32 CUDA points [N, d] with K centres through
+    ``kpp_lloyd_prepare`` / ``kpp_lloyd_step``: the workspace holds the
+    points' BF16 split, prepared once."""
+
+    def __init__(self, points, K: int):
+        import torch
+
+        if not points.is_cuda or points.dtype != torch.float32:
+            raise ValueError("points must be a float32 CUDA tensor")
+        self.points = points.contiguous()
+        self.N, self.d = self.points.shape
+        self.K = int(K)
+        dev = self.points.device
+        with torch.cuda.device(dev):
+            n = kpp_lloyd_workspace_size(self.N, self.d, self.K)
+            if n == 0:
+                raise KppError(ERR_INVALID_ARG, "kpp_lloyd_workspace_size")
+            self.ws = torch.empty(n, dtype=torch.uint8, device=dev)
+            st = kpp_lloyd_prepare(self.points.data_ptr(), self.N, self.d, self.K,
+                                   self.ws.data_ptr(), self.ws.numel(), _stream_handle(dev))
+        if st != OK:
+            raise KppError(st, "kpp_lloyd_prepare")
+
+    def assign(self, centres, labels=None):
+        """Labels int32 [N] of the nearest centre (``kpp_lloyd_assign``)."""
+        import torch
+
+        dev = self.points.device
+        c = centres.to(device=dev, dtype=torch.float32).contiguous()
+        labels = labels if labels is not None else torch.empty(self.N, dtype=torch.int32,
+                                                               device=dev)
+        with torch.cuda.device(dev):
+            st = kpp_lloyd_assign(c.data_ptr(), self.N, self.d, self.K, labels.data_ptr(),
+                                  self.ws.data_ptr(), self.ws.numel(), _stream_handle(dev))
+        if st != OK:
+            raise KppError(st, "kpp_lloyd_assign")
+        return labels
+
+    def step(self, centres, check: bool = True):
+        """One iteration from ``centres`` [K, d] float32 (CUDA).  Returns
+        ``(labels int32 [N], d2 float32 [N], new centres [K, d], counts int64
+        [K], phi float64 [1])``."""
+        import torch
+
+        dev = self.points.device
+        c = centres.to(device=dev, dtype=torch.float32).contiguous()
+        labels = torch.empty(self.N, dtype=torch.int32, device=dev)
+        d2 = torch.empty(self.N, dtype=torch.float32, device=dev)
+        out = torch.empty_like(c)
+        counts = torch.empty(self.K, dtype=torch.int64, device=dev)
+        phi = torch.empty(1, dtype=torch.float64, device=dev)
+        with torch.cuda.device(dev):
+            sh = _stream_handle(dev)
+            st = kpp_lloyd_step(self.points.data_ptr(), self.N, self.d, c.data_ptr(), self.K,
+                                labels.data_ptr(), d2.data_ptr(), out.data_ptr(),
+                                counts.data_ptr(), phi.data_ptr(), self.ws.data_ptr(),
+                                self.ws.numel(), sh)
+            if st != OK:
+                raise KppError(st, "kpp_lloyd_step")
+            if check:
+                st = kpp_read_status(self.ws.data_ptr(), sh)
+                if st != OK:
+                    raise KppError(st, "kpp_lloyd_step (device)")
+        return labels, d2, out, counts, phi
 
 
 def seed_host(points_host, K: int, seed: int, stream_id: int = 0, *, dtype=None,

@@ -1,0 +1,712 @@
+// kpp_lloyd.cu -- one Lloyd iteration on the GPU: the clustering stage the
+// seeds are for (Section II: "the clustering part is implemented the same as
+// the K-means algorithm", i.e. Lloyd's nearest-centre assignment followed by
+// moving every centre to the mean of its points).
+//
+// Assignment is a dense contraction: the nearest centre of x minimises
+// |c|^2 - 2 x.c, so the N x K dot products run on the tensor cores
+// (tcgen05.mma, BF16 operands staged by TMA, FP32 accumulators in tensor
+// memory).  To keep close to FP32 accuracy every operand is split into two
+// BF16 planes, v = hi + lo with hi = bf16(v) and lo = bf16(v - hi), and the
+// product is hi.hi + hi.lo + lo.hi (the dropped lo.lo term is ~2^-16 of the
+// whole).  The epilogue reads the accumulators from tensor memory and keeps
+// the running minimum of |c_k|^2 - 2 x.c_k per point (smallest k on ties).
+//
+// The update reads the FP32 points again: the exact squared distance to the
+// assigned centre in the same FP32 difference form as the seeding pass, the
+// cost phi, and per-centre sums (FP32 per CTA in shared memory, FP64 across
+// CTAs) and counts; centres with no point keep their position.
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+
+#include <cstring>
+#include <mutex>
+
+#include "kpp.h"
+#include "kpp_internal.h"
+#include "kpp_tc.cuh"
+
+namespace kpp {
+namespace {
+
+constexpr int kBM = 128;      // points per tile: TMEM lanes of an accumulator
+constexpr int kMT = 2;        // point tiles served by each pass over the centres
+constexpr int kBN = 128;      // centres per tile: accumulator columns
+constexpr int kBK = 64;       // features per chunk: one 128-byte swizzled row of BF16
+constexpr int kMaxD = 128;    // d <= 128 (at most two chunks)
+constexpr int kMaxK = 4096;   // centre norms stay in shared memory
+constexpr int kThreads = 256; // warp 0 TMA, warp 1 MMA, warp 2 TMEM, warps 4-7 epilogue
+constexpr int kMaxStages = 4; // centre-tile stages in flight
+constexpr uint32_t kTmemCols = 2 * kMT * kBN; // [buffer][point tile] accumulators: 512
+constexpr uint32_t kABytes = kBM * kBK * 2; // one plane, one chunk: 16 KB
+constexpr uint32_t kBBytes = kBN * kBK * 2; // 16 KB
+constexpr size_t kAlign = 256;
+
+size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+struct Layout {
+    int dp;   // padded feature count (64 or 128)
+    int grid; // CTAs of the per-point kernels
+    size_t off_phi, off_plo, off_chi, off_clo, off_cn, off_sums, off_counts, off_partial, bytes;
+};
+
+bool shape_ok(int64_t N, int32_t d, int32_t K)
+{
+    return N >= 1 && N < (int64_t(1) << 31) && d >= 1 && d <= kMaxD && K >= 1 && K <= kMaxK &&
+           K <= N;
+}
+
+Layout layout(int64_t N, int32_t d, int32_t K)
+{
+    Layout L;
+    L.dp = d <= 64 ? 64 : 128;
+    L.grid = 1024;
+    size_t off = sizeof(Control);
+    L.off_phi = off = round_up(off, kAlign);
+    off += (size_t)N * L.dp * 2;
+    L.off_plo = off = round_up(off, kAlign);
+    off += (size_t)N * L.dp * 2;
+    L.off_chi = off = round_up(off, kAlign);
+    off += (size_t)K * L.dp * 2;
+    L.off_clo = off = round_up(off, kAlign);
+    off += (size_t)K * L.dp * 2;
+    L.off_cn = off = round_up(off, kAlign);
+    off += (size_t)K * 4;
+    L.off_sums = off = round_up(off, kAlign);
+    off += (size_t)K * d * 8;
+    L.off_counts = off = round_up(off, kAlign);
+    off += (size_t)K * 8;
+    L.off_partial = off = round_up(off, kAlign);
+    off += (size_t)L.grid * 8;
+    L.bytes = round_up(off, kAlign);
+    return L;
+}
+
+// ---------------------------------------------------------------------------
+// Splitting into BF16 planes (zero-padded to dp features).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void split_bf16(float v, __nv_bfloat16 &hi, __nv_bfloat16 &lo)
+{
+    hi = __float2bfloat16_rn(v);
+    lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+}
+
+__global__ void split_rows_kernel(const float *x, int64_t rows, int d, int dp, __nv_bfloat16 *hi,
+                                  __nv_bfloat16 *lo)
+{
+    const int64_t n = rows * dp;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = e / dp;
+        const int j = (int)(e - r * dp);
+        const float v = j < d ? x[r * d + j] : 0.f;
+        split_bf16(v, hi[e], lo[e]);
+    }
+}
+
+// |c_k|^2 in FP32 (one thread per centre)
+__global__ void centre_norms_kernel(const float *c, int K, int d, float *cn)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= K)
+        return;
+    float s = 0.f;
+    for (int j = 0; j < d; ++j)
+        s = fmaf(c[(int64_t)k * d + j], c[(int64_t)k * d + j], s);
+    cn[k] = s;
+}
+
+// ---------------------------------------------------------------------------
+// Assignment on the tensor cores.
+// ---------------------------------------------------------------------------
+struct AssignArgs {
+    int64_t N;
+    int32_t K;
+    int32_t nk;     // feature chunks (dp / 64)
+    int32_t stages; // centre-tile stages in shared memory
+    const float *cn;
+    int32_t *labels;
+    Control *ctl;
+    uint64_t timeout_ns;
+};
+
+__device__ __forceinline__ void fail(Control *ctl, volatile int *abort_flag)
+{
+    *abort_flag = 1;
+    atomicCAS(&ctl->status, KPP_OK, KPP_ERR_TIMEOUT);
+}
+
+// Persistent over groups of kMT 128-point tiles.  Per group the producer
+// loads both BF16 planes of its points once, then streams both planes of
+// every 128-centre tile, one 64-feature chunk at a time, through a ring of
+// shared-memory stages; each stage feeds the MMAs of all kMT point tiles, so
+// a centre byte read from L2 serves 256 points.  The MMA thread accumulates
+// hi.hi + hi.lo + lo.hi into one of two sets of tensor-memory accumulators;
+// the four epilogue warps turn a finished set into running argmins while the
+// next one fills.  Every wait is bounded: on a timeout the kernel records
+// KPP_ERR_TIMEOUT, lets the copies and MMAs already issued finish (again
+// bounded), frees its tensor memory and returns.
+__global__ void __launch_bounds__(kThreads, 1)
+    lloyd_assign_kernel(const __grid_constant__ CUtensorMap map_phi,
+                        const __grid_constant__ CUtensorMap map_plo,
+                        const __grid_constant__ CUtensorMap map_chi,
+                        const __grid_constant__ CUtensorMap map_clo, AssignArgs a)
+{
+    using namespace tc;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                                ~uintptr_t(1023));
+    const int NS = a.stages;
+    uint8_t *sA = smem;                              // [tile][plane][chunk] 16 KB each
+    uint8_t *sB = smem + kMT * 2 * a.nk * kABytes;   // [stage][plane] 16 KB each
+    float *s_cn = reinterpret_cast<float *>(sB + NS * 2 * kBBytes);
+    __shared__ uint64_t a_full, a_empty, b_full[kMaxStages], b_empty[kMaxStages], acc_full[2],
+        acc_empty[2], done;
+    __shared__ uint32_t tmem_base;
+    __shared__ volatile int abort_flag;
+    auto a_tile = [&](int t, int plane, int k) { return sA + ((t * 2 + plane) * a.nk + k) * kABytes; };
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        mbar_init(&a_full, 1);
+        mbar_init(&a_empty, 1);
+        for (int s = 0; s < NS; ++s) {
+            mbar_init(&b_full[s], 1);
+            mbar_init(&b_empty[s], 1);
+        }
+        for (int s = 0; s < 2; ++s) {
+            mbar_init(&acc_full[s], 1);
+            mbar_init(&acc_empty[s], kBM);
+        }
+        mbar_init(&done, 1);
+        fence_mbar_init();
+        abort_flag = 0;
+    }
+    // centre norms, padded with +infinity up to whole centre tiles (those
+    // columns can never win)
+    const int n_ct = (a.K + kBN - 1) / kBN;
+    for (int k = threadIdx.x; k < n_ct * kBN; k += blockDim.x)
+        s_cn[k] = k < a.K ? a.cn[k] : __int_as_float(0x7f800000);
+    if (warp == 2)
+        tmem_alloc(&tmem_base, kTmemCols);
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+
+    const int64_t n_mt = (a.N + kBM - 1) / kBM;
+    const int64_t n_grp = (n_mt + kMT - 1) / kMT;
+    const uint32_t tmem = tmem_base;
+
+    if (warp == 0 && lane == 0) {
+        // ---- producer ----
+        uint32_t it = 0, g = 0;
+        uint32_t a_pending = 0; // 1 + iteration of the last point load issued
+        uint32_t b_pending[kMaxStages] = {}; // 1 + use of the last centre load per stage
+        for (int64_t gp = blockIdx.x; gp < n_grp && !abort_flag; gp += gridDim.x, ++it) {
+            if (it > 0 && !mbar_wait(&a_empty, (it - 1) & 1, a.timeout_ns)) {
+                fail(a.ctl, &abort_flag);
+                break;
+            }
+            mbar_expect_tx(&a_full, kMT * 2 * a.nk * kABytes);
+            for (int t = 0; t < kMT; ++t) {
+                const int y = (int)((gp * kMT + t) * kBM);
+                for (int k = 0; k < a.nk; ++k) {
+                    tma_load_2d(a_tile(t, 0, k), &map_phi, &a_full, k * kBK, y);
+                    tma_load_2d(a_tile(t, 1, k), &map_plo, &a_full, k * kBK, y);
+                }
+            }
+            a_pending = it + 1;
+            for (int ct = 0; ct < n_ct && !abort_flag; ++ct) {
+                for (int k = 0; k < a.nk; ++k, ++g) {
+                    const uint32_t s = g % NS, use = g / NS;
+                    if (use > 0 && !mbar_wait(&b_empty[s], (use - 1) & 1, a.timeout_ns)) {
+                        fail(a.ctl, &abort_flag);
+                        break;
+                    }
+                    mbar_expect_tx(&b_full[s], 2 * kBBytes);
+                    tma_load_2d(sB + (s * 2 + 0) * kBBytes, &map_chi, &b_full[s], k * kBK, ct * kBN);
+                    tma_load_2d(sB + (s * 2 + 1) * kBBytes, &map_clo, &b_full[s], k * kBK, ct * kBN);
+                    b_pending[s] = use + 1;
+                }
+            }
+        }
+        if (abort_flag) {
+            // let the copies already issued land before the CTA exits
+            if (a_pending)
+                mbar_wait(&a_full, (a_pending - 1) & 1, a.timeout_ns);
+            for (int s = 0; s < NS; ++s)
+                if (b_pending[s])
+                    mbar_wait(&b_full[s], (b_pending[s] - 1) & 1, a.timeout_ns);
+        }
+    } else if (warp == 1 && lane == 0) {
+        // ---- MMA issuer ----
+        const uint32_t idesc = idesc_bf16_f32(kBM, kBN);
+        uint32_t it = 0, g = 0, t = 0;
+        bool issued = false;
+        for (int64_t gp = blockIdx.x; gp < n_grp && !abort_flag; gp += gridDim.x, ++it) {
+            if (!mbar_wait(&a_full, it & 1, a.timeout_ns)) {
+                fail(a.ctl, &abort_flag);
+                break;
+            }
+            fence_after_sync();
+            for (int ct = 0; ct < n_ct && !abort_flag; ++ct, ++t) {
+                const uint32_t buf = t & 1, ause = t >> 1;
+                if (ause > 0 && !mbar_wait(&acc_empty[buf], (ause - 1) & 1, a.timeout_ns)) {
+                    fail(a.ctl, &abort_flag);
+                    break;
+                }
+                fence_after_sync();
+                for (int k = 0; k < a.nk; ++k, ++g) {
+                    const uint32_t s = g % NS, use = g / NS;
+                    if (!mbar_wait(&b_full[s], use & 1, a.timeout_ns)) {
+                        fail(a.ctl, &abort_flag);
+                        break;
+                    }
+                    fence_after_sync();
+                    const uint32_t bh = smem_u32(sB + (s * 2 + 0) * kBBytes);
+                    const uint32_t bl = smem_u32(sB + (s * 2 + 1) * kBBytes);
+#pragma unroll
+                    for (int mt = 0; mt < kMT; ++mt) {
+                        const uint32_t d_tmem = tmem + (buf * kMT + mt) * kBN;
+                        const uint32_t ah = smem_u32(a_tile(mt, 0, k));
+                        const uint32_t al = smem_u32(a_tile(mt, 1, k));
+#pragma unroll
+                        for (int kk = 0; kk < kBK / 16; ++kk) {
+                            // one MMA covers 16 features = 32 bytes of the swizzled row
+                            const uint32_t o = kk * 32;
+                            mma_bf16(d_tmem, sdesc_k_sw128(ah + o), sdesc_k_sw128(bh + o), idesc,
+                                     (k | kk) ? 1u : 0u);
+                            mma_bf16(d_tmem, sdesc_k_sw128(ah + o), sdesc_k_sw128(bl + o), idesc, 1u);
+                            mma_bf16(d_tmem, sdesc_k_sw128(al + o), sdesc_k_sw128(bh + o), idesc, 1u);
+                        }
+                    }
+                    issued = true;
+                    mma_commit(&b_empty[s]); // stage s is free once these are done
+                }
+                if (abort_flag)
+                    break;
+                mma_commit(&acc_full[buf]);
+            }
+            if (abort_flag)
+                break;
+            mma_commit(&a_empty);
+        }
+        // every MMA issued has completed before the tensor memory is freed
+        if (issued) {
+            mma_commit(&done);
+            mbar_wait(&done, 0, a.timeout_ns);
+        }
+    } else if (warp >= 4) {
+        // ---- epilogue: argmin of |c|^2 - 2 x.c over the centres ----
+        const int q = warp & 3; // this warp's quarter of the TMEM lanes
+        const int row_local = q * 32 + lane;
+        uint32_t t = 0;
+        for (int64_t gp = blockIdx.x; gp < n_grp && !abort_flag; gp += gridDim.x) {
+            float best[kMT];
+            int bk[kMT];
+#pragma unroll
+            for (int mt = 0; mt < kMT; ++mt) {
+                best[mt] = __int_as_float(0x7f800000);
+                bk[mt] = 0;
+            }
+            for (int ct = 0; ct < n_ct; ++ct, ++t) {
+                const uint32_t buf = t & 1, use = t >> 1;
+                if (!mbar_wait(&acc_full[buf], use & 1, a.timeout_ns)) {
+                    fail(a.ctl, &abort_flag);
+                    break;
+                }
+                fence_after_sync();
+                const float4 *cn4 = reinterpret_cast<const float4 *>(s_cn + ct * kBN);
+#pragma unroll
+                for (int mt = 0; mt < kMT; ++mt) {
+                    const uint32_t base = tmem + (buf * kMT + mt) * kBN + ((uint32_t)(q * 32) << 16);
+                    // the tile's 128 columns, two loads in flight at a time
+#pragma unroll 1
+                    for (int h = 0; h < 4; h += 2) {
+                        uint32_t r[2][32];
+                        tmem_ld32_async(base + h * 32, r[0]);
+                        tmem_ld32_async(base + h * 32 + 32, r[1]);
+                        tmem_ld_wait();
+#pragma unroll
+                        for (int c = 0; c < 2; ++c) {
+#pragma unroll
+                            for (int v = 0; v < 8; ++v) {
+                                const float4 n4 = cn4[(h + c) * 8 + v];
+                                const float nv[4] = {n4.x, n4.y, n4.z, n4.w};
+#pragma unroll
+                                for (int e = 0; e < 4; ++e) {
+                                    const int i = v * 4 + e;
+                                    const float sc = fmaf(-2.f, __uint_as_float(r[c][i]), nv[e]);
+                                    if (sc < best[mt]) {
+                                        best[mt] = sc;
+                                        bk[mt] = ct * kBN + (h + c) * 32 + i;
+                                    }
+                                }
+                            }
+                        }
+                    }
+                }
+                fence_before_sync();
+                mbar_arrive(&acc_empty[buf]);
+            }
+            if (abort_flag)
+                break;
+#pragma unroll
+            for (int mt = 0; mt < kMT; ++mt) {
+                const int64_t row = (gp * kMT + mt) * kBM + row_local;
+                if (row < a.N)
+                    a.labels[row] = bk[mt];
+            }
+        }
+    }
+    fence_before_sync();
+    __syncthreads();
+    if (warp == 2) {
+        fence_after_sync();
+        tmem_dealloc(tmem, kTmemCols);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Update: exact D^2 to the assigned centre, phi, per-centre sums and counts.
+// ---------------------------------------------------------------------------
+constexpr int kUpdThreads = 512;
+constexpr size_t kUpdSmem = 200 * 1024; // per-CTA FP32 sums of one centre tile
+
+// centres per tile of the update's shared-memory sums
+__host__ __device__ inline int update_tile(int K, int d)
+{
+    const int t = (int)((kUpdSmem - 4 * 1024) / ((size_t)d * 4 + 4));
+    return t < K ? t : K;
+}
+
+// Every CTA owns a contiguous range of points and walks it once per tile of
+// TK centres.  A warp takes kUpdRows points at a time: their labels in one
+// load, then all their features (lane j holds features j, j+32, ...), so the
+// loads of a batch are in flight together; each point's features are added
+// into the CTA's FP32 sums of its centre in shared memory.  The tile's sums
+// then go to the FP64 totals in global memory with one atomic per (centre,
+// feature).  The first walk also takes the FP32 difference-form D^2 to the
+// assigned centre (the seeding pass's arithmetic: even and odd features in
+// two accumulators) and the CTA's cost in a fixed order.
+constexpr int kUpdRows = 8;
+constexpr int kUpdVec = kMaxD / 32; // features per lane and point
+
+__global__ void __launch_bounds__(kUpdThreads, 1)
+    lloyd_update_kernel(const float *x, int64_t N, int d, int K, const float *c,
+                        const int32_t *labels, float *d2_out, double *sums,
+                        unsigned long long *counts, double *partial)
+{
+    extern __shared__ float u_smem[];
+    __shared__ double wsum[kUpdThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwarps = blockDim.x >> 5;
+    const int TK = update_tile(K, d);
+    float *acc = u_smem;                                                   // [TK x d]
+    unsigned *cnt = reinterpret_cast<unsigned *>(u_smem + (size_t)TK * d); // [TK]
+    const int64_t per = (N + gridDim.x - 1) / gridDim.x;
+    const int64_t r0 = blockIdx.x * per;
+    const int64_t r1 = (r0 + per) < N ? (r0 + per) : N;
+    double mine = 0.0; // lane 0: this warp's cost
+    for (int k0 = 0; k0 < K; k0 += TK) {
+        const int tk = (K - k0) < TK ? (K - k0) : TK;
+        for (int e = threadIdx.x; e < tk * d; e += blockDim.x)
+            acc[e] = 0.f;
+        for (int e = threadIdx.x; e < tk; e += blockDim.x)
+            cnt[e] = 0u;
+        __syncthreads();
+        for (int64_t b = r0 + (int64_t)warp * kUpdRows; b < r1; b += (int64_t)nwarps * kUpdRows) {
+            const int nr = (r1 - b) < kUpdRows ? (int)(r1 - b) : kUpdRows;
+            const int my_label = lane < nr ? labels[b + lane] : 0;
+            float xv[kUpdRows][kUpdVec];
+#pragma unroll
+            for (int q = 0; q < kUpdRows; ++q)
+#pragma unroll
+                for (int t = 0; t < kUpdVec; ++t) {
+                    const int j = lane + 32 * t;
+                    xv[q][t] = (q < nr && j < d) ? x[(b + q) * d + j] : 0.f;
+                }
+            // first walk: the assigned centres' features too, all in flight
+            float cv[kUpdRows][kUpdVec];
+            if (k0 == 0) {
+#pragma unroll
+                for (int q = 0; q < kUpdRows; ++q) {
+                    const int k = __shfl_sync(0xffffffffu, my_label, q);
+#pragma unroll
+                    for (int t = 0; t < kUpdVec; ++t) {
+                        const int j = lane + 32 * t;
+                        cv[q][t] = (q < nr && j < d) ? c[(int64_t)k * d + j] : 0.f;
+                    }
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < kUpdRows; ++q) {
+                if (q >= nr)
+                    break;
+                const int k = __shfl_sync(0xffffffffu, my_label, q);
+                if (k0 == 0) {
+                    // features j = lane + 32t: even j into a0, odd into a1
+                    float a0 = 0.f, a1 = 0.f;
+#pragma unroll
+                    for (int t = 0; t < kUpdVec; ++t) {
+                        const int j = lane + 32 * t;
+                        if (j < d) {
+                            const float u = xv[q][t] - cv[q][t];
+                            if (j & 1)
+                                a1 = fmaf(u, u, a1);
+                            else
+                                a0 = fmaf(u, u, a0);
+                        }
+                    }
+                    float v = a0 + a1;
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1)
+                        v += __shfl_xor_sync(0xffffffffu, v, o);
+                    if (lane == 0) {
+                        if (d2_out)
+                            d2_out[b + q] = v;
+                        mine += (double)v;
+                    }
+                }
+                if (k >= k0 && k < k0 + tk) {
+                    float *ak = acc + (size_t)(k - k0) * d;
+#pragma unroll
+                    for (int t = 0; t < kUpdVec; ++t) {
+                        const int j = lane + 32 * t;
+                        if (j < d)
+                            atomicAdd(ak + j, xv[q][t]);
+                    }
+                    if (lane == 0)
+                        atomicAdd(cnt + (k - k0), 1u);
+                }
+            }
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < tk * d; e += blockDim.x) {
+            const float v = acc[e];
+            if (v != 0.f)
+                atomicAdd(sums + (size_t)k0 * d + e, (double)v);
+        }
+        for (int e = threadIdx.x; e < tk; e += blockDim.x)
+            if (cnt[e])
+                atomicAdd(counts + k0 + e, (unsigned long long)cnt[e]);
+        __syncthreads();
+    }
+    // the CTA's cost: warps in order
+    if (lane == 0)
+        wsum[warp] = mine;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < nwarps; ++w)
+            t += wsum[w];
+        partial[blockIdx.x] = t;
+    }
+}
+
+__global__ void lloyd_finalize_kernel(const float *c_in, int K, int d, const double *sums,
+                                      const unsigned long long *counts, float *c_out,
+                                      int64_t *counts_out, const double *partial, int nparts,
+                                      double *phi_out)
+{
+    const int64_t n = (int64_t)K * d;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int k = (int)(e / d);
+        const unsigned long long m = counts[k];
+        c_out[e] = m ? (float)(sums[e] / (double)m) : c_in[e];
+    }
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; counts_out && k < K;
+         k += gridDim.x * blockDim.x)
+        counts_out[k] = (int64_t)counts[k];
+    if (blockIdx.x == 0 && threadIdx.x == 0 && phi_out) {
+        double s = 0.0;
+        for (int b = 0; b < nparts; ++b)
+            s += partial[b];
+        *phi_out = s;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Host side.
+// ---------------------------------------------------------------------------
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
+{
+    static std::once_flag once;
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+// [rows x dp] BF16, 128-byte swizzled boxes of 64 features x box_rows rows;
+// rows past the end read as zero
+bool make_map(CUtensorMap *m, const void *base, int64_t rows, int dp, int box_rows)
+{
+    auto enc = encode_fn();
+    if (!enc)
+        return false;
+    cuuint64_t dims[2] = {(cuuint64_t)dp, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)dp * 2};
+    cuuint32_t box[2] = {(cuuint32_t)kBK, (cuuint32_t)box_rows};
+    cuuint32_t es[2] = {1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box,
+               es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// centre-tile stages that fit beside the point tiles and the centre norms
+int padded_k(int K) { return (K + kBN - 1) / kBN * kBN; }
+
+int assign_stages(int nk, int K)
+{
+    const size_t budget =
+        227 * 1024 - 1024 - 256 - (size_t)kMT * 2 * nk * kABytes - (size_t)padded_k(K) * 4;
+    const int s = (int)(budget / (2 * kBBytes));
+    return s < kMaxStages ? s : kMaxStages;
+}
+
+size_t assign_smem(int nk, int K)
+{
+    return 1024 + (size_t)kMT * 2 * nk * kABytes + (size_t)assign_stages(nk, K) * 2 * kBBytes +
+           (size_t)padded_k(K) * 4;
+}
+
+int sm_count()
+{
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return 0;
+    return sms;
+}
+
+} // namespace
+} // namespace kpp
+
+using namespace kpp;
+
+extern "C" {
+
+size_t kpp_lloyd_workspace_size(int64_t N, int32_t d, int32_t K)
+{
+    if (!shape_ok(N, d, K))
+        return 0;
+    return layout(N, d, K).bytes;
+}
+
+kpp_status kpp_lloyd_prepare(const float *points, int64_t N, int32_t d, int32_t K, void *workspace,
+                             size_t workspace_bytes, kpp_stream_t stream)
+{
+    if (!points || !shape_ok(N, d, K))
+        return KPP_ERR_INVALID_ARG;
+    const Layout L = layout(N, d, K);
+    if (!workspace || (reinterpret_cast<uintptr_t>(workspace) % kAlign) != 0 ||
+        workspace_bytes < L.bytes)
+        return KPP_ERR_WORKSPACE;
+    char *ws = reinterpret_cast<char *>(workspace);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const int sms = sm_count();
+    if (sms <= 0)
+        return KPP_ERR_CUDA;
+    split_rows_kernel<<<sms * 8, 256, 0, s>>>(points, N, d, L.dp,
+                                             reinterpret_cast<__nv_bfloat16 *>(ws + L.off_phi),
+                                             reinterpret_cast<__nv_bfloat16 *>(ws + L.off_plo));
+    return cudaGetLastError() == cudaSuccess ? KPP_OK : KPP_ERR_LAUNCH;
+}
+
+kpp_status kpp_lloyd_assign(const float *centres, int64_t N, int32_t d, int32_t K,
+                            int32_t *labels_out, void *workspace, size_t workspace_bytes,
+                            kpp_stream_t stream)
+{
+    if (!centres || !labels_out || !shape_ok(N, d, K))
+        return KPP_ERR_INVALID_ARG;
+    const Layout L = layout(N, d, K);
+    if (!workspace || (reinterpret_cast<uintptr_t>(workspace) % kAlign) != 0 ||
+        workspace_bytes < L.bytes)
+        return KPP_ERR_WORKSPACE;
+    char *ws = reinterpret_cast<char *>(workspace);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const int sms = sm_count();
+    if (sms <= 0)
+        return KPP_ERR_CUDA;
+    auto *phi = reinterpret_cast<__nv_bfloat16 *>(ws + L.off_phi);
+    auto *plo = reinterpret_cast<__nv_bfloat16 *>(ws + L.off_plo);
+    auto *chi = reinterpret_cast<__nv_bfloat16 *>(ws + L.off_chi);
+    auto *clo = reinterpret_cast<__nv_bfloat16 *>(ws + L.off_clo);
+    float *cn = reinterpret_cast<float *>(ws + L.off_cn);
+    CUtensorMap m_phi, m_plo, m_chi, m_clo;
+    if (!make_map(&m_phi, phi, N, L.dp, kBM) || !make_map(&m_plo, plo, N, L.dp, kBM) ||
+        !make_map(&m_chi, chi, K, L.dp, kBN) || !make_map(&m_clo, clo, K, L.dp, kBN))
+        return KPP_ERR_CUDA;
+    const int nk = L.dp / kBK;
+    const size_t smem = assign_smem(nk, K);
+    if (cudaFuncSetAttribute(lloyd_assign_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess)
+        return KPP_ERR_CUDA;
+    AssignArgs a;
+    a.N = N;
+    a.K = K;
+    a.nk = nk;
+    a.stages = assign_stages(nk, K);
+    a.cn = cn;
+    a.labels = labels_out;
+    a.ctl = reinterpret_cast<Control *>(ws);
+    a.timeout_ns = 2000000000ull;
+    if (a.stages < 2)
+        return KPP_ERR_UNSUPPORTED;
+    if (cudaMemsetAsync(ws, 0, sizeof(Control), s) != cudaSuccess)
+        return KPP_ERR_CUDA;
+    split_rows_kernel<<<(K * L.dp + 255) / 256, 256, 0, s>>>(centres, K, d, L.dp, chi, clo);
+    centre_norms_kernel<<<(K + 127) / 128, 128, 0, s>>>(centres, K, d, cn);
+    const int64_t n_grp = ((N + kBM - 1) / kBM + kMT - 1) / kMT;
+    const int grid = (int)(n_grp < sms ? n_grp : sms);
+    lloyd_assign_kernel<<<grid, kThreads, smem, s>>>(m_phi, m_plo, m_chi, m_clo, a);
+    return cudaGetLastError() == cudaSuccess ? KPP_OK : KPP_ERR_LAUNCH;
+}
+
+kpp_status kpp_lloyd_step(const float *points, int64_t N, int32_t d, const float *centres,
+                          int32_t K, int32_t *labels_out, float *d2_out, float *centres_out,
+                          int64_t *counts_out, double *phi_out, void *workspace,
+                          size_t workspace_bytes, kpp_stream_t stream)
+{
+    if (!points || !centres || !labels_out || !centres_out || !shape_ok(N, d, K))
+        return KPP_ERR_INVALID_ARG;
+    const Layout L = layout(N, d, K);
+    if (!workspace || (reinterpret_cast<uintptr_t>(workspace) % kAlign) != 0 ||
+        workspace_bytes < L.bytes)
+        return KPP_ERR_WORKSPACE;
+    char *ws = reinterpret_cast<char *>(workspace);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const int sms = sm_count();
+    if (sms <= 0)
+        return KPP_ERR_CUDA;
+    double *sums = reinterpret_cast<double *>(ws + L.off_sums);
+    auto *counts = reinterpret_cast<unsigned long long *>(ws + L.off_counts);
+    double *partial = reinterpret_cast<double *>(ws + L.off_partial);
+    const size_t usmem = (size_t)update_tile(K, d) * ((size_t)d * 4 + 4);
+    if (cudaFuncSetAttribute(lloyd_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)usmem) != cudaSuccess)
+        return KPP_ERR_CUDA;
+    const kpp_status st =
+        kpp_lloyd_assign(centres, N, d, K, labels_out, workspace, workspace_bytes, stream);
+    if (st != KPP_OK)
+        return st;
+    if (cudaMemsetAsync(ws + L.off_sums, 0, L.off_partial - L.off_sums, s) != cudaSuccess)
+        return KPP_ERR_CUDA;
+    const int ugrid = sms < L.grid ? sms : L.grid;
+    lloyd_update_kernel<<<ugrid, kUpdThreads, usmem, s>>>(points, N, d, K, centres, labels_out,
+                                                          d2_out, sums, counts, partial);
+    lloyd_finalize_kernel<<<(K * d + 255) / 256, 256, 0, s>>>(centres, K, d, sums, counts,
+                                                              centres_out, counts_out, partial,
+                                                              ugrid, phi_out);
+    return cudaGetLastError() == cudaSuccess ? KPP_OK : KPP_ERR_LAUNCH;
+}
+
+} // extern "C"

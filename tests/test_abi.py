@@ -31,7 +31,9 @@ def test_header_declares_the_boundary():
     for required in ["kpp_seed", "kpp_workspace_size", "kpp_read_status", "kpp_quantize",
                      "kpp_seed_host", "kpp_status_string", "kpp_version", "kpp_describe",
                      "kpp_seed_batched", "kpp_batch_workspace_size", "kpp_seed_noalloc",
-                     "kpp_tune", "kpp_tune_workspace_size", "kpp_tune_clear"]:
+                     "kpp_tune", "kpp_tune_workspace_size", "kpp_tune_clear",
+                     "kpp_lloyd_workspace_size", "kpp_lloyd_prepare", "kpp_lloyd_step",
+                     "kpp_lloyd_assign"]:
         assert required in names
 
 

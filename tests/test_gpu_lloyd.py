@@ -1,0 +1,130 @@
+"""GPU parity of one Lloyd iteration (kpp_lloyd_step, through the C ABI)
+against the FP64 oracle's Lloyd step:
+
+* integer coordinates (|x| <= 64): the split BF16 operands are exact, so the
+  tensor-core scores are exact and labels, D^2, counts and the cost must be
+  bit-identical to the oracle, centres equal to its FP64 means rounded once;
+* Gaussian mixtures: every label is the oracle's or within the stated
+  near-tie bound of it (counted), D^2 within 1e-5 of the FP64 distance to
+  the chosen centre, centres within 1e-5 of the FP64 means of the GPU's own
+  assignment, the cost within 1e-5;
+* ragged N (not a multiple of the 128-point tile, fewer points than one
+  tile), K across centre tiles and a partial last tile, d below, at and
+  between the 64-feature chunks, empty clusters, several iterations, and
+  argument errors.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_1908_02136_gb300 as kpp
+from paper_1908_02136_gb300 import datagen
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda:0"
+
+
+def _step(x_np, C_np):
+    x = torch.from_numpy(x_np).to(DEV)
+    ll = kpp.Lloyd(x, C_np.shape[0])
+    lab, d2, C2, cnt, phi = ll.step(torch.from_numpy(C_np.astype(np.float32)))
+    torch.cuda.synchronize()
+    return (lab.cpu().numpy(), d2.cpu().numpy(), C2.cpu().numpy(), cnt.cpu().numpy(),
+            float(phi.cpu()[0]))
+
+
+def _check_float(x_np, C_np, max_event_frac=0.05):
+    lab, d2, C2, cnt, phi = _step(x_np, C_np)
+    C64 = C_np.astype(np.float32).astype(np.float64)
+    ref = oracle.lloyd_step(x_np, C64)
+    X = x_np.astype(np.float64)
+    N = X.shape[0]
+    # every label is the oracle's, or a near tie within the bound
+    dist_g = ((X - C64[lab]) ** 2).sum(1)
+    dist_o = ref["d2"]
+    diff = lab != ref["labels"]
+    bound = 2.0 ** -12 * np.linalg.norm(X, axis=1) * np.linalg.norm(C64, axis=1).max() + 1e-30
+    assert np.all(dist_g[diff] - dist_o[diff] <= bound[diff]), (dist_g[diff] - dist_o[diff]).max()
+    assert diff.sum() <= max(2, max_event_frac * N), diff.sum()
+    # D^2: FP32 difference form to the chosen centre
+    nz = dist_g > 0
+    assert np.all(d2[~nz] == 0)
+    assert np.max(np.abs(d2[nz] - dist_g[nz]) / dist_g[nz]) <= 1e-5
+    # counts and centres from the GPU's own assignment
+    K = C64.shape[0]
+    assert np.array_equal(cnt, np.bincount(lab, minlength=K))
+    sums = np.zeros_like(C64)
+    np.add.at(sums, lab, X)
+    means = np.where(cnt[:, None] > 0, sums / np.maximum(cnt, 1)[:, None], C64)
+    # per-CTA sums are FP32 (a few hundred points each), totals FP64
+    np.testing.assert_allclose(C2, means, rtol=1e-5, atol=1e-5 * np.abs(means).max())
+    assert phi == pytest.approx(dist_g.sum(), rel=1e-5)
+    return diff.sum()
+
+
+@pytest.mark.parametrize("N,d,K", [(1000, 8, 7), (5000, 64, 256), (4999, 128, 300),
+                                   (127, 16, 5), (20000, 100, 1000), (3000, 2, 1)])
+def test_integer_regime_bit_identical(N, d, K):
+    x = datagen.integer_points(N, d, seed=N + d, n_comp=8)
+    C = x[np.random.default_rng(K).choice(N, K, replace=False)].astype(np.float64)
+    lab, d2, C2, cnt, phi = _step(x, C)
+    ref = oracle.lloyd_step(x, C)
+    assert np.array_equal(lab, ref["labels"])
+    # the assignment entry point alone gives the same labels
+    ll = kpp.Lloyd(torch.from_numpy(x).to(DEV), K)
+    assert np.array_equal(ll.assign(torch.from_numpy(C.astype(np.float32))).cpu().numpy(), lab)
+    assert np.array_equal(d2.astype(np.float64), ref["d2"])
+    assert np.array_equal(cnt, ref["counts"])
+    assert phi == ref["phi"]
+    assert np.array_equal(C2, ref["centres"].astype(np.float32))
+
+
+@pytest.mark.parametrize("N,d,K", [(20000, 32, 64), (30011, 64, 512), (10000, 128, 257),
+                                   (8000, 48, 40)])
+def test_float_regime(N, d, K):
+    x = datagen.gmm(N, d, K, seed=d)
+    C = x[np.random.default_rng(1).choice(N, K, replace=False)].astype(np.float64)
+    _check_float(x, C)
+
+
+def test_empty_clusters_keep_their_centre():
+    x = datagen.gmm(3000, 16, 4, seed=3)
+    C = np.concatenate([x[:4].astype(np.float64), np.full((3, 16), 1e4)])
+    lab, d2, C2, cnt, phi = _step(x, C)
+    assert np.all(cnt[4:] == 0)
+    assert np.array_equal(C2[4:], C[4:].astype(np.float32))
+
+
+def test_iterations_lower_the_cost():
+    x_np = datagen.gmm(50_000, 32, 32, seed=9)
+    x = torch.from_numpy(x_np).to(DEV)
+    idx, _, _ = kpp.seed(x, 32, 1)
+    C = x[idx]
+    ll = kpp.Lloyd(x, 32)
+    phis = []
+    for _ in range(6):
+        lab, d2, C, cnt, phi = ll.step(C)
+        phis.append(float(phi.cpu()[0]))
+    assert all(b <= a * (1 + 1e-6) for a, b in zip(phis, phis[1:]))
+    assert phis[-1] < phis[0]
+
+
+def test_argument_errors():
+    x = torch.zeros((100, 200), device=DEV)
+    with pytest.raises(kpp.KppError) as e:
+        kpp.Lloyd(x, 4)
+    assert e.value.status == kpp.ERR_INVALID_ARG
+    assert kpp.kpp_lloyd_workspace_size(100, 8, 5000) == 0
+    assert kpp.kpp_lloyd_workspace_size(10, 8, 11) == 0
+    x = torch.zeros((100, 8), device=DEV)
+    ll = kpp.Lloyd(x, 4)
+    small = torch.empty(256, dtype=torch.uint8, device=DEV)
+    c = torch.zeros((4, 8), device=DEV)
+    lab = torch.empty(100, dtype=torch.int32, device=DEV)
+    with torch.cuda.device(DEV):
+        st = kpp.kpp_lloyd_step(x.data_ptr(), 100, 8, c.data_ptr(), 4, lab.data_ptr(), None,
+                                torch.empty_like(c).data_ptr(), None, None, small.data_ptr(),
+                                small.numel(), None)
+    assert st == kpp.ERR_WORKSPACE
