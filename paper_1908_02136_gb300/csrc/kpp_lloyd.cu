@@ -387,18 +387,20 @@ __host__ __device__ inline int update_tile(int K, int d)
 // into the CTA's FP32 sums of its centre in shared memory.  The tile's sums
 // then go to the FP64 totals in global memory with one atomic per (centre,
 // feature).  The first walk also takes the FP32 difference-form D^2 to the
-// assigned centre (the seeding pass's arithmetic: even and odd features in
-// two accumulators) and the CTA's cost in a fixed order.
+// assigned centre and the CTA's cost: per lane the squares of its features
+// (even features in one accumulator, odd in another), then the batch's 8
+// per-lane partials are reduce-scattered across the warp (9 shuffles for 8
+// points) and lane 4r holds the D^2 of point r; costs are FP32 two-sum pairs.
 constexpr int kUpdRows = 8;
-constexpr int kUpdVec = kMaxD / 32; // features per lane and point
 
+template <int VEC> // features per lane and point: ceil(d / 32)
 __global__ void __launch_bounds__(kUpdThreads, 1)
     lloyd_update_kernel(const float *x, int64_t N, int d, int K, const float *c,
                         const int32_t *labels, float *d2_out, double *sums,
                         unsigned long long *counts, double *partial)
 {
     extern __shared__ float u_smem[];
-    __shared__ double wsum[kUpdThreads / 32];
+    __shared__ float2 wsum[kUpdThreads / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nwarps = blockDim.x >> 5;
     const int TK = update_tile(K, d);
@@ -407,7 +409,7 @@ __global__ void __launch_bounds__(kUpdThreads, 1)
     const int64_t per = (N + gridDim.x - 1) / gridDim.x;
     const int64_t r0 = blockIdx.x * per;
     const int64_t r1 = (r0 + per) < N ? (r0 + per) : N;
-    double mine = 0.0; // lane 0: this warp's cost
+    Pair mine{}; // the cost of this lane's points (lanes 0, 4, ..., 28)
     for (int k0 = 0; k0 < K; k0 += TK) {
         const int tk = (K - k0) < TK ? (K - k0) : TK;
         for (int e = threadIdx.x; e < tk * d; e += blockDim.x)
@@ -418,25 +420,56 @@ __global__ void __launch_bounds__(kUpdThreads, 1)
         for (int64_t b = r0 + (int64_t)warp * kUpdRows; b < r1; b += (int64_t)nwarps * kUpdRows) {
             const int nr = (r1 - b) < kUpdRows ? (int)(r1 - b) : kUpdRows;
             const int my_label = lane < nr ? labels[b + lane] : 0;
-            float xv[kUpdRows][kUpdVec];
+            float xv[kUpdRows][VEC];
 #pragma unroll
             for (int q = 0; q < kUpdRows; ++q)
 #pragma unroll
-                for (int t = 0; t < kUpdVec; ++t) {
+                for (int t = 0; t < VEC; ++t) {
                     const int j = lane + 32 * t;
                     xv[q][t] = (q < nr && j < d) ? x[(b + q) * d + j] : 0.f;
                 }
-            // first walk: the assigned centres' features too, all in flight
-            float cv[kUpdRows][kUpdVec];
             if (k0 == 0) {
+                // the assigned centres' features, all in flight, then the
+                // per-lane partial squared distances of the 8 points
+                float part[kUpdRows];
 #pragma unroll
                 for (int q = 0; q < kUpdRows; ++q) {
                     const int k = __shfl_sync(0xffffffffu, my_label, q);
+                    float a0 = 0.f, a1 = 0.f;
 #pragma unroll
-                    for (int t = 0; t < kUpdVec; ++t) {
+                    for (int t = 0; t < VEC; ++t) {
                         const int j = lane + 32 * t;
-                        cv[q][t] = (q < nr && j < d) ? c[(int64_t)k * d + j] : 0.f;
+                        const float cj = (q < nr && j < d) ? c[(int64_t)k * d + j] : 0.f;
+                        const float u = xv[q][t] - cj;
+                        if (j & 1)
+                            a1 = fmaf(u, u, a1);
+                        else
+                            a0 = fmaf(u, u, a0);
                     }
+                    part[q] = a0 + a1;
+                }
+                // reduce-scatter: lane bits 4, 3, 2 select the point, bits 1, 0
+                // are summed last; lane 4r ends with point r's D^2
+#pragma unroll
+                for (int h = 0; h < 3; ++h) {
+                    const int m = 16 >> h;     // 16, 8, 4
+                    const int w = 4 >> h;      // values kept: 4, 2, 1
+                    const bool up = (lane & m) != 0;
+#pragma unroll
+                    for (int i = 0; i < w; ++i) {
+                        const float send = up ? part[i] : part[i + w];
+                        const float keep = up ? part[i + w] : part[i];
+                        part[i] = keep + __shfl_xor_sync(0xffffffffu, send, m);
+                    }
+                }
+                float v = part[0];
+                v += __shfl_xor_sync(0xffffffffu, v, 2);
+                v += __shfl_xor_sync(0xffffffffu, v, 1);
+                const int r = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
+                if ((lane & 3) == 0 && r < nr) {
+                    if (d2_out)
+                        d2_out[b + r] = v;
+                    mine.add(v);
                 }
             }
 #pragma unroll
@@ -444,34 +477,10 @@ __global__ void __launch_bounds__(kUpdThreads, 1)
                 if (q >= nr)
                     break;
                 const int k = __shfl_sync(0xffffffffu, my_label, q);
-                if (k0 == 0) {
-                    // features j = lane + 32t: even j into a0, odd into a1
-                    float a0 = 0.f, a1 = 0.f;
-#pragma unroll
-                    for (int t = 0; t < kUpdVec; ++t) {
-                        const int j = lane + 32 * t;
-                        if (j < d) {
-                            const float u = xv[q][t] - cv[q][t];
-                            if (j & 1)
-                                a1 = fmaf(u, u, a1);
-                            else
-                                a0 = fmaf(u, u, a0);
-                        }
-                    }
-                    float v = a0 + a1;
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1)
-                        v += __shfl_xor_sync(0xffffffffu, v, o);
-                    if (lane == 0) {
-                        if (d2_out)
-                            d2_out[b + q] = v;
-                        mine += (double)v;
-                    }
-                }
                 if (k >= k0 && k < k0 + tk) {
                     float *ak = acc + (size_t)(k - k0) * d;
 #pragma unroll
-                    for (int t = 0; t < kUpdVec; ++t) {
+                    for (int t = 0; t < VEC; ++t) {
                         const int j = lane + 32 * t;
                         if (j < d)
                             atomicAdd(ak + j, xv[q][t]);
@@ -492,16 +501,29 @@ __global__ void __launch_bounds__(kUpdThreads, 1)
                 atomicAdd(counts + k0 + e, (unsigned long long)cnt[e]);
         __syncthreads();
     }
-    // the CTA's cost: warps in order
+    // the CTA's cost: lanes, then warps, in a fixed order
+    const Pair wt = warp_pair_sum(mine);
     if (lane == 0)
-        wsum[warp] = mine;
+        wsum[warp] = make_float2(wt.hi, wt.lo);
     __syncthreads();
     if (threadIdx.x == 0) {
-        double t = 0.0;
+        Pair t{};
         for (int w = 0; w < nwarps; ++w)
-            t += wsum[w];
-        partial[blockIdx.x] = t;
+            t.add(Pair{wsum[w].x, wsum[w].y});
+        partial[blockIdx.x] = (double)t.hi + (double)t.lo;
     }
+}
+
+using UpdateFn = void (*)(const float *, int64_t, int, int, const float *, const int32_t *,
+                          float *, double *, unsigned long long *, double *);
+
+UpdateFn update_fn(int d)
+{
+    if (d <= 32)
+        return &lloyd_update_kernel<1>;
+    if (d <= 64)
+        return &lloyd_update_kernel<2>;
+    return &lloyd_update_kernel<4>;
 }
 
 __global__ void lloyd_finalize_kernel(const float *c_in, int K, int d, const double *sums,
@@ -691,8 +713,9 @@ kpp_status kpp_lloyd_step(const float *points, int64_t N, int32_t d, const float
     auto *counts = reinterpret_cast<unsigned long long *>(ws + L.off_counts);
     double *partial = reinterpret_cast<double *>(ws + L.off_partial);
     const size_t usmem = (size_t)update_tile(K, d) * ((size_t)d * 4 + 4);
-    if (cudaFuncSetAttribute(lloyd_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)usmem) != cudaSuccess)
+    const UpdateFn ufn = update_fn(d);
+    if (cudaFuncSetAttribute(ufn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)usmem) !=
+        cudaSuccess)
         return KPP_ERR_CUDA;
     const kpp_status st =
         kpp_lloyd_assign(centres, N, d, K, labels_out, workspace, workspace_bytes, stream);
@@ -701,8 +724,8 @@ kpp_status kpp_lloyd_step(const float *points, int64_t N, int32_t d, const float
     if (cudaMemsetAsync(ws + L.off_sums, 0, L.off_partial - L.off_sums, s) != cudaSuccess)
         return KPP_ERR_CUDA;
     const int ugrid = sms < L.grid ? sms : L.grid;
-    lloyd_update_kernel<<<ugrid, kUpdThreads, usmem, s>>>(points, N, d, K, centres, labels_out,
-                                                          d2_out, sums, counts, partial);
+    ufn<<<ugrid, kUpdThreads, usmem, s>>>(points, N, d, K, centres, labels_out, d2_out, sums,
+                                          counts, partial);
     lloyd_finalize_kernel<<<(K * d + 255) / 256, 256, 0, s>>>(centres, K, d, sums, counts,
                                                               centres_out, counts_out, partial,
                                                               ugrid, phi_out);
