@@ -624,7 +624,8 @@ def main():
     if pst != kpp.OK:
         raise kpp.KppError(pst, "kpp_describe")
     plan = plan.as_dict()
-    form_name = {kpp.FORM_STREAMED: "streamed", kpp.FORM_PERSISTENT: "persistent"}[plan["form"]]
+    form_name = {kpp.FORM_STREAMED: "streamed", kpp.FORM_PERSISTENT: "persistent",
+                 kpp.FORM_RECOMPUTE: "recompute"}[plan["form"]]
     ws = kpp.workspace_for(N, d, K, code, dev, opts)
     idx = torch.empty(K, dtype=torch.int64, device=dev)
     d2 = torch.empty(N, dtype=torch.float32, device=dev)
@@ -730,7 +731,8 @@ def main():
     d2_bytes = 8 * N if form_name == "streamed" else 0  # D^2 stays on chip when persistent
     alg_bytes = passes_per_launch * (point_bytes + d2_bytes)
     achieved = alg_bytes / (per_launch_ms / 1e3) / 1e9
-    traffic = profiled_traffic(form_name, wl.name, args.dtype, plan)
+    traffic = (profiled_traffic(form_name, wl.name, args.dtype, plan)
+               if form_name in KERNEL_SOURCES else None)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic,
                 "peak_source": "measured" if peaks else "fallback",

@@ -82,7 +82,11 @@ typedef enum {
 typedef enum {
     KPP_FORM_AUTO = 0,
     KPP_FORM_STREAMED = 1,   /* one kernel per seed, captured in a CUDA graph */
-    KPP_FORM_PERSISTENT = 2  /* one cooperative launch for all K passes */
+    KPP_FORM_PERSISTENT = 2, /* one cooperative launch for all K passes */
+    KPP_FORM_RECOMPUTE = 3   /* for comparison only: the paper's own step (Section II),
+                                every pass recomputes each point's distance to all
+                                seeds chosen so far (O(N K^2 d) work) in the streamed
+                                form's launches; results identical to the streamed form */
 } kpp_form;
 
 /* Tuning knobs; a zeroed struct (or NULL) means "choose automatically". */

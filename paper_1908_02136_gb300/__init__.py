@@ -26,7 +26,7 @@ import threading
 from . import build as _build
 
 F32, BF16, FP8_E4M3 = 0, 1, 2
-FORM_AUTO, FORM_STREAMED, FORM_PERSISTENT = 0, 1, 2
+FORM_AUTO, FORM_STREAMED, FORM_PERSISTENT, FORM_RECOMPUTE = 0, 1, 2, 3
 (OK, ERR_INVALID_ARG, ERR_CUDA, ERR_LAUNCH, ERR_TIMEOUT, ERR_DEGENERATE,
  ERR_WORKSPACE, ERR_UNSUPPORTED) = range(8)
 

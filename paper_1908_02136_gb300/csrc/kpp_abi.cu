@@ -209,6 +209,12 @@ kpp_status make_plan(int64_t N, int32_t d, int32_t K, int dt, const kpp_options 
     switch (o.form) {
     case KPP_FORM_STREAMED:
         return plan_streamed(N, d, dt, o, sms, pl);
+    case KPP_FORM_RECOMPUTE: {
+        const kpp_status st = plan_streamed(N, d, dt, o, sms, pl);
+        if (st == KPP_OK)
+            pl->form = KPP_FORM_RECOMPUTE;
+        return st;
+    }
     case KPP_FORM_PERSISTENT:
         return plan_persistent(N, d, K, dt, o, sms, pl);
     case KPP_FORM_AUTO: {
@@ -449,6 +455,7 @@ kpp_status kpp_seed(const void *points, const float *row_scales, int64_t N, int3
         p.seg_sums = reinterpret_cast<float2 *>(ws + pl.off_seg);
     }
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    p.recompute = pl.form == KPP_FORM_RECOMPUTE ? 1 : 0;
     if (pl.form == KPP_FORM_PERSISTENT)
         return run_persistent(pl, p, s);
     const int use_graph = opts ? opts->use_graph : 0;

@@ -54,6 +54,8 @@ struct Problem {
     float2 *seg_sums;   // streamed form: [nblocks * nseg] pair sums of the pass
     unsigned long long *slots; // persistent form: [2][nblocks * kSlotWords] tagged block sums
     unsigned long long *mail;  // persistent form: the drawn index, tagged with its pass
+    int32_t recompute;         // streamed form: every pass rebuilds D^2 from all chosen seeds
+    int32_t pad_;
 };
 
 // ---------------------------------------------------------------------------

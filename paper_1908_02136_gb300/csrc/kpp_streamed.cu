@@ -144,17 +144,24 @@ __global__ void __launch_bounds__(kStreamThreads)
     const int64_t ci = pass_centre(p, m);
     if (ci < 0)
         return;
-    CentreRegs<DT, D, L> cr;
-    cr.load(p.points, p.scales, ci);
     PassIO io{};
     io.r0 = (int64_t)blockIdx.x * p.chunk;
     io.r1 = (io.r0 + p.chunk) < p.N ? (io.r0 + p.chunk) : p.N;
-    io.first = (m == 0);
     io.gpts = reinterpret_cast<const char *>(p.points);
     io.scales = p.scales;
     io.d2 = p.d2;
     io.segs = p.seg_sums + (int64_t)blockIdx.x * p.nseg;
-    const Pair w = pass_rows<DT, D, L, D2_INPLACE>(io, cr);
+    // The paper's own step (Section II) recomputes every point's distance to
+    // all seeds chosen so far; the incremental form takes only the newest.
+    // Both keep the minimum of the same FP32 distances, so D^2 is identical.
+    Pair w{};
+    for (int j = p.recompute ? 0 : m; j <= m; ++j) {
+        const int64_t cj = (j == m) ? ci : __ldcg(p.idx + j);
+        CentreRegs<DT, D, L> cr;
+        cr.load(p.points, p.scales, cj);
+        io.first = (j == 0);
+        w = pass_rows<DT, D, L, D2_INPLACE>(io, cr);
+    }
     finish_pass(p, m, w);
 }
 
@@ -166,17 +173,22 @@ __global__ void __launch_bounds__(kStreamThreads)
     const int64_t ci = pass_centre(p, m);
     if (ci < 0)
         return;
-    load_centre_smem<DT>(p.points, p.scales, ci, p.d, c_sh);
-    __syncthreads();
     PassIO io{};
     io.r0 = (int64_t)blockIdx.x * p.chunk;
     io.r1 = (io.r0 + p.chunk) < p.N ? (io.r0 + p.chunk) : p.N;
-    io.first = (m == 0);
     io.gpts = reinterpret_cast<const char *>(p.points);
     io.scales = p.scales;
     io.d2 = p.d2;
     io.segs = p.seg_sums + (int64_t)blockIdx.x * p.nseg;
-    const Pair w = pass_rows_generic<DT>(io, p.d, c_sh);
+    Pair w{};
+    for (int j = p.recompute ? 0 : m; j <= m; ++j) {
+        const int64_t cj = (j == m) ? ci : __ldcg(p.idx + j);
+        __syncthreads(); // the previous centre is no longer read
+        load_centre_smem<DT>(p.points, p.scales, cj, p.d, c_sh);
+        __syncthreads();
+        io.first = (j == 0);
+        w = pass_rows_generic<DT>(io, p.d, c_sh);
+    }
     finish_pass(p, m, w);
 }
 
