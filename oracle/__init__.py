@@ -99,6 +99,21 @@ def _load():
         lib.kpp_oracle_lloyd_step.argtypes = [
             P, P, ctypes.c_int, ctypes.c_int64, ctypes.c_int32, P, ctypes.c_int32, P, P, P, P, P]
         lib.kpp_oracle_lloyd_step.restype = ctypes.c_int
+        U64, I64, I32, D = ctypes.c_uint64, ctypes.c_int64, ctypes.c_int32, ctypes.c_double
+        lib.kpp_oracle_uniform_ctr.argtypes = [U64] * 6
+        lib.kpp_oracle_uniform_ctr.restype = D
+        lib.kpp_oracle_min_update.argtypes = [P, P, ctypes.c_int, I64, I32, P, I64, P, ctypes.c_int]
+        lib.kpp_oracle_min_update.restype = D
+        lib.kpp_oracle_kmpar_select.argtypes = [P, I64, D, D, U64, U64, I32, P, P, P]
+        lib.kpp_oracle_kmpar_select.restype = I64
+        lib.kpp_oracle_kmpar_weights.argtypes = [P, P, ctypes.c_int, I64, I32, P, I64, P]
+        lib.kpp_oracle_kmpar_weights.restype = None
+        lib.kpp_oracle_weighted_seed.argtypes = [P, P, ctypes.c_int, I32, P, I64, P, I32, U64, U64,
+                                                 P, I32, P, P]
+        lib.kpp_oracle_weighted_seed.restype = ctypes.c_int
+        lib.kpp_oracle_kmeans_par.argtypes = [P, P, ctypes.c_int, I64, I32, I32, D, I32, U64, U64,
+                                              P, P, I64, P, P]
+        lib.kpp_oracle_kmeans_par.restype = ctypes.c_int
         _lib = lib
         return lib
 
@@ -244,3 +259,86 @@ def lloyd_step(points: np.ndarray, centres: np.ndarray, *, dtype=None,
     if st != OK:
         raise ValueError(f"kpp_oracle_lloyd_step: status {st}")
     return {"labels": labels, "d2": d2, "centres": out, "counts": counts, "phi": phi.value}
+
+
+# ---------------------------------------------------------------------------
+# k-means|| (readings P1-P4 in kpp_oracle.c).
+# ---------------------------------------------------------------------------
+def uniform_ctr(seed: int, stream: int, c0: int, c1: int = 0, c2: int = 0, c3: int = 0) -> float:
+    """Word 0 of Philox4x64-10 at counter (c0, c1, c2, c3), mapped to [0, 1)."""
+    return _load().kpp_oracle_uniform_ctr(seed, stream, c0, c1, c2, c3)
+
+
+def _stored(points, dtype, scales):
+    pts = np.ascontiguousarray(points)
+    code = _dtype_code(pts, dtype)
+    sc = None if scales is None else np.ascontiguousarray(scales, dtype=np.float32)
+    return pts, code, sc
+
+
+def min_update(points, centres, D2=None, *, dtype=None, scales=None):
+    """D^2 = min(D2, squared distance to the listed centre indices) in FP64;
+    D2=None starts from +infinity.  Returns (D2, phi)."""
+    pts, code, sc = _stored(points, dtype, scales)
+    N, d = pts.shape
+    c = np.ascontiguousarray(centres, dtype=np.int64)
+    init = D2 is None
+    out = np.empty(N, dtype=np.float64) if init else np.array(D2, dtype=np.float64)
+    phi = _load().kpp_oracle_min_update(_ptr(pts), _ptr(sc), code, N, d, _ptr(c), c.size,
+                                        _ptr(out), 1 if init else 0)
+    return out, phi
+
+
+def kmpar_select(D2, phi: float, ell: float, seed: int, stream: int, r: int):
+    """Round r's Bernoulli decisions: (flags uint8, p, u) per point."""
+    D = np.ascontiguousarray(D2, dtype=np.float64)
+    N = D.size
+    flags = np.empty(N, dtype=np.uint8)
+    p = np.empty(N, dtype=np.float64)
+    u = np.empty(N, dtype=np.float64)
+    _load().kpp_oracle_kmpar_select(_ptr(D), N, phi, ell, seed, stream, r, _ptr(flags), _ptr(p),
+                                    _ptr(u))
+    return flags, p, u
+
+
+def kmpar_weights(points, cand, *, dtype=None, scales=None):
+    """Number of points whose nearest candidate is each candidate."""
+    pts, code, sc = _stored(points, dtype, scales)
+    N, d = pts.shape
+    c = np.ascontiguousarray(cand, dtype=np.int64)
+    w = np.empty(c.size, dtype=np.int64)
+    _load().kpp_oracle_kmpar_weights(_ptr(pts), _ptr(sc), code, N, d, _ptr(c), c.size, _ptr(w))
+    return w
+
+
+def weighted_seed(points, cand, w, K: int, seed: int, stream: int = 0, *, dtype=None,
+                  scales=None, forced=None):
+    """Weighted k-means++ over the candidates (P4): (positions, own draws, status)."""
+    pts, code, sc = _stored(points, dtype, scales)
+    d = pts.shape[1]
+    c = np.ascontiguousarray(cand, dtype=np.int64)
+    ww = np.ascontiguousarray(w, dtype=np.int64)
+    fo = None if forced is None else np.ascontiguousarray(forced, dtype=np.int64)
+    out = np.empty(K, dtype=np.int64)
+    own = np.empty(K, dtype=np.int64)
+    st = _load().kpp_oracle_weighted_seed(_ptr(pts), _ptr(sc), code, d, _ptr(c), c.size, _ptr(ww),
+                                          K, seed, stream, _ptr(fo),
+                                          0 if fo is None else fo.size, _ptr(out), _ptr(own))
+    return out, own, st
+
+
+def kmeans_par(points, K: int, ell: float, rounds: int, seed: int, stream: int = 0, *,
+               dtype=None, scales=None, cand_cap: int | None = None) -> dict:
+    """k-means|| (P1-P4): chosen point indices, the candidate list, its weights."""
+    pts, code, sc = _stored(points, dtype, scales)
+    N, d = pts.shape
+    cap = cand_cap if cand_cap is not None else min(N, 1 + int(rounds * ell * 4) + 64)
+    idx = np.empty(K, dtype=np.int64)
+    cand = np.empty(cap, dtype=np.int64)
+    w = np.empty(cap, dtype=np.int64)
+    nc = ctypes.c_int64()
+    st = _load().kpp_oracle_kmeans_par(_ptr(pts), _ptr(sc), code, N, d, K, float(ell), rounds,
+                                       seed, stream, _ptr(idx), _ptr(cand), cap,
+                                       ctypes.byref(nc), _ptr(w))
+    n = nc.value
+    return {"status": st, "idx": idx, "cand": cand[:n].copy(), "w": w[:n].copy()}

@@ -60,6 +60,24 @@
  *   L3  phi = sum_i of the assigned squared distances (FP64, index order),
  *       the cost of the assignment, before the update.
  *
+ * k-means|| (the oversampling initialisation of Bahmani et al., the
+ * technique the paper cites as an alternative to k-means++):
+ *   P1  c_0 = the first seed of R2; D^2 = squared distance to it, phi = sum.
+ *   P2  For rounds r = 0 .. R-1: point i joins the candidates iff
+ *       u_{r,i} < ell * D^2_i / phi, with u_{r,i} = Philox4x64-10(key = {seed,
+ *       stream}, counter = {i, r + 1, 0, 0}), word 0 mapped as in R1 (a point
+ *       already chosen has D^2 = 0 and is never chosen again).  The round's
+ *       new candidates are appended in increasing point index; D^2 then takes
+ *       the minimum over them and phi is recomputed (FP64).
+ *   P3  Weight of candidate c = the number of points whose nearest candidate
+ *       is c (the earliest candidate in list order on a tie).
+ *   P4  Recluster: weighted k-means++ over the candidates in list order --
+ *       the first centre by inverse CDF on the weights, then by inverse CDF
+ *       on w_c * D^2_c (D^2 to the centres chosen so far), rules of R3, with
+ *       draws v_m = Philox4x64-10(key = {seed, stream}, counter = {m, 0, 1,
+ *       0}) word 0 mapped as in R1.  Fewer than K candidates with weight, or
+ *       a zero total, is a degenerate stop (R4).
+ *
  * Build: gcc -O2 -ffp-contract=off -shared -fPIC (no fused multiply-add, so
  * the arithmetic is the one written here on every host).
  */
@@ -456,4 +474,211 @@ int kpp_oracle_lloyd_step(const void *points, const float *scales, int dtype, in
     free(sum);
     free(cnt);
     return KPP_ORACLE_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* k-means|| (readings P1-P4).                                                */
+/* ------------------------------------------------------------------------ */
+
+/* A uniform in [0, 1) from word 0 of Philox at an explicit counter. */
+double kpp_oracle_uniform_ctr(uint64_t seed, uint64_t stream, uint64_t c0, uint64_t c1,
+                              uint64_t c2, uint64_t c3)
+{
+    const uint64_t ctr[4] = {c0, c1, c2, c3};
+    const uint64_t key[2] = {seed, stream};
+    uint64_t out[4];
+    kpp_oracle_philox4x64_10(ctr, key, out);
+    return (double)(out[0] >> 11) * (1.0 / 9007199254740992.0);
+}
+
+/* FP64 squared distance between point i and point j (decoded, R5). */
+static double sqdist(const void *pts, const float *scales, int dtype, int32_t d, int64_t i,
+                     int64_t j)
+{
+    double s = 0.0;
+    for (int32_t k = 0; k < d; ++k) {
+        double t = coord(pts, scales, dtype, i, d, k) - coord(pts, scales, dtype, j, d, k);
+        s += t * t;
+    }
+    return s;
+}
+
+/* D2[i] = min(D2[i], min over the listed centres of the distance to them);
+ * with init != 0 D2 starts at +infinity.  Returns the sum (index order). */
+double kpp_oracle_min_update(const void *points, const float *scales, int dtype, int64_t N,
+                             int32_t d, const int64_t *centres, int64_t n, double *D2, int init)
+{
+    double phi = 0.0;
+    for (int64_t i = 0; i < N; ++i) {
+        double best = init ? INFINITY : D2[i];
+        for (int64_t c = 0; c < n; ++c) {
+            double v = sqdist(points, scales, dtype, d, i, centres[c]);
+            if (v < best)
+                best = v;
+        }
+        D2[i] = best;
+        phi += best;
+    }
+    return phi;
+}
+
+/* Round r's Bernoulli decisions (P2): flags[i] = 1 iff u_{r,i} < ell D2[i] / phi;
+ * p_out[i] (may be NULL) = ell D2[i] / phi, u_out[i] (may be NULL) = u_{r,i}.
+ * Returns the number selected. */
+int64_t kpp_oracle_kmpar_select(const double *D2, int64_t N, double phi, double ell,
+                                uint64_t seed, uint64_t stream, int32_t r, uint8_t *flags,
+                                double *p_out, double *u_out)
+{
+    int64_t n = 0;
+    for (int64_t i = 0; i < N; ++i) {
+        double p = phi > 0.0 ? ell * D2[i] / phi : 0.0;
+        double u = kpp_oracle_uniform_ctr(seed, stream, (uint64_t)i, (uint64_t)r + 1, 0, 0);
+        flags[i] = u < p ? 1 : 0;
+        n += flags[i];
+        if (p_out)
+            p_out[i] = p;
+        if (u_out)
+            u_out[i] = u;
+    }
+    return n;
+}
+
+/* Weights (P3): w[c] = number of points whose nearest candidate is cand[c]. */
+void kpp_oracle_kmpar_weights(const void *points, const float *scales, int dtype, int64_t N,
+                              int32_t d, const int64_t *cand, int64_t nc, int64_t *w)
+{
+    for (int64_t c = 0; c < nc; ++c)
+        w[c] = 0;
+    for (int64_t i = 0; i < N; ++i) {
+        int64_t best = 0;
+        double best_d = INFINITY;
+        for (int64_t c = 0; c < nc; ++c) {
+            double v = sqdist(points, scales, dtype, d, i, cand[c]);
+            if (v < best_d) {
+                best_d = v;
+                best = c;
+            }
+        }
+        w[best] += 1;
+    }
+}
+
+/* Recluster (P4): weighted k-means++ over the candidates; out[m] = position in
+ * cand of centre m (-1 after a degenerate stop).  forced (may be NULL) replays
+ * the first n_forced positions; own_out[m] (may be NULL) = the oracle's own
+ * draw at step m. */
+int kpp_oracle_weighted_seed(const void *points, const float *scales, int dtype, int32_t d,
+                             const int64_t *cand, int64_t nc, const int64_t *w, int32_t K,
+                             uint64_t seed, uint64_t stream, const int64_t *forced,
+                             int32_t n_forced, int64_t *out, int64_t *own_out)
+{
+    if (K < 1 || nc < 1)
+        return KPP_ORACLE_INVALID;
+    double *D2 = (double *)malloc(sizeof(double) * (size_t)nc);
+    double *val = (double *)malloc(sizeof(double) * (size_t)nc);
+    if (!D2 || !val) {
+        free(D2);
+        free(val);
+        return KPP_ORACLE_INVALID;
+    }
+    int status = KPP_ORACLE_OK;
+    for (int32_t m = 0; m < K; ++m)
+        out[m] = -1;
+    for (int64_t c = 0; c < nc; ++c) {
+        D2[c] = INFINITY;
+        val[c] = (double)w[c];
+    }
+    for (int32_t m = 0; m < K; ++m) {
+        double v = kpp_oracle_uniform_ctr(seed, stream, (uint64_t)m, 0, 1, 0);
+        double t, T;
+        int64_t own = kpp_oracle_pick(val, nc, v, &t, &T);
+        if (own_out)
+            own_out[m] = own;
+        if (T == 0.0) {
+            status = KPP_ORACLE_DEGENERATE;
+            break;
+        }
+        int64_t taken = m < n_forced ? forced[m] : own;
+        if (taken < 0 || taken >= nc) {
+            status = KPP_ORACLE_INVALID;
+            break;
+        }
+        out[m] = taken;
+        for (int64_t c = 0; c < nc; ++c) {
+            double dd = sqdist(points, scales, dtype, d, cand[c], cand[taken]);
+            if (dd < D2[c])
+                D2[c] = dd;
+            val[c] = (double)w[c] * D2[c];
+        }
+    }
+    free(D2);
+    free(val);
+    return status;
+}
+
+/*
+ * The whole of k-means|| (P1-P4).  cand_out has room for cand_cap indices;
+ * n_cand_out gets the number of candidates (the run stops with
+ * KPP_ORACLE_INVALID if they do not fit).  idx_out [K]: the chosen points.
+ */
+int kpp_oracle_kmeans_par(const void *points, const float *scales, int dtype, int64_t N,
+                          int32_t d, int32_t K, double ell, int32_t rounds, uint64_t seed,
+                          uint64_t stream, int64_t *idx_out, int64_t *cand_out, int64_t cand_cap,
+                          int64_t *n_cand_out, int64_t *w_out)
+{
+    if (!points || N < 1 || d < 1 || K < 1 || K > N || rounds < 0 || !(ell > 0.0) ||
+        !idx_out || !cand_out || cand_cap < 1)
+        return KPP_ORACLE_INVALID;
+    double *D2 = (double *)malloc(sizeof(double) * (size_t)N);
+    uint8_t *flags = (uint8_t *)malloc((size_t)N);
+    if (!D2 || !flags) {
+        free(D2);
+        free(flags);
+        return KPP_ORACLE_INVALID;
+    }
+    int status = KPP_ORACLE_OK;
+    double u0 = kpp_oracle_uniform(seed, stream, 0);
+    int64_t c0 = (int64_t)floor(u0 * (double)N);
+    if (c0 > N - 1)
+        c0 = N - 1;
+    int64_t nc = 0;
+    cand_out[nc++] = c0;
+    double phi = kpp_oracle_min_update(points, scales, dtype, N, d, &c0, 1, D2, 1);
+    for (int32_t r = 0; r < rounds && status == KPP_ORACLE_OK; ++r) {
+        kpp_oracle_kmpar_select(D2, N, phi, ell, seed, stream, r, flags, NULL, NULL);
+        int64_t first = nc;
+        for (int64_t i = 0; i < N; ++i) {
+            if (!flags[i])
+                continue;
+            if (nc >= cand_cap) {
+                status = KPP_ORACLE_INVALID;
+                break;
+            }
+            cand_out[nc++] = i;
+        }
+        if (status != KPP_ORACLE_OK)
+            break;
+        phi = kpp_oracle_min_update(points, scales, dtype, N, d, cand_out + first, nc - first,
+                                    D2, 0);
+    }
+    int64_t *w = (int64_t *)malloc(sizeof(int64_t) * (size_t)(nc > 0 ? nc : 1));
+    int64_t *pos = (int64_t *)malloc(sizeof(int64_t) * (size_t)K);
+    if (status == KPP_ORACLE_OK && w && pos) {
+        kpp_oracle_kmpar_weights(points, scales, dtype, N, d, cand_out, nc, w);
+        status = kpp_oracle_weighted_seed(points, scales, dtype, d, cand_out, nc, w, K, seed,
+                                          stream, NULL, 0, pos, NULL);
+        for (int32_t m = 0; m < K; ++m)
+            idx_out[m] = pos[m] >= 0 ? cand_out[pos[m]] : -1;
+        if (w_out)
+            memcpy(w_out, w, sizeof(int64_t) * (size_t)nc);
+    } else if (status == KPP_ORACLE_OK) {
+        status = KPP_ORACLE_INVALID;
+    }
+    if (n_cand_out)
+        *n_cand_out = nc;
+    free(w);
+    free(pos);
+    free(D2);
+    free(flags);
+    return status;
 }
