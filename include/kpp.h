@@ -69,7 +69,8 @@ typedef enum {
     KPP_ERR_TIMEOUT = 4,     /* a bounded device wait gave up (device status) */
     KPP_ERR_DEGENERATE = 5,  /* sum D^2 = 0 before K seeds (device status) */
     KPP_ERR_WORKSPACE = 6,   /* workspace NULL, misaligned or too small */
-    KPP_ERR_UNSUPPORTED = 7  /* option combination not built */
+    KPP_ERR_UNSUPPORTED = 7, /* option combination not built */
+    KPP_ERR_CAPACITY = 8     /* k-means||: more candidates than the caller's room */
 } kpp_status;
 
 /* Storage type of the points; distances are always accumulated in FP32. */
@@ -323,6 +324,55 @@ KPP_API kpp_status kpp_lloyd_step(const float *points, int64_t N, int32_t d,
                                   float *d2_out, float *centres_out, int64_t *counts_out,
                                   double *phi_out, void *workspace, size_t workspace_bytes,
                                   kpp_stream_t stream);
+
+/*
+ * k-means|| -- the oversampling initialisation of Bahmani et al., which the
+ * paper cites as the parallel alternative to k-means++ (Section I):
+ *   1. c_0 = the first k-means++ seed, min(floor(u_0 N), N - 1) with u_0 the
+ *      Philox draw of kpp_seed; D^2 = squared distance to it, phi = sum D^2.
+ *   2. For rounds r = 0 .. rounds-1: point i joins the candidates iff
+ *      u_{r,i} < ell D^2_i / phi, evaluated in FP64 on the stored FP32 D^2,
+ *      with u_{r,i} = Philox4x64-10(key {seed, stream_id}, counter {i, r + 1,
+ *      0, 0}) mapped like u_m.  The round's new candidates are appended in
+ *      increasing point index; D^2 then takes the minimum over them and phi
+ *      is summed again (FP64).
+ *   3. Weight of a candidate = the number of points whose nearest candidate
+ *      it is (the earliest in list order on a tie).
+ *   4. Recluster: weighted k-means++ over the candidates in list order, on
+ *      w_c (first centre) and then w_c D^2_c, draws from Philox counter
+ *      {m, 0, 1, 0}, inverse CDF as in kpp_seed.
+ * Arguments:
+ *   points      [N x d] FP32 device, d <= 128, 1 <= K <= N < 2^31
+ *   ell         expected candidates per round (> 0; e.g. 2K)
+ *   rounds      >= 0 oversampling rounds (e.g. 5)
+ *   cand_cap    room of cand_out / weights_out (>= 1)
+ *   idx_out     [K] int64 device: the chosen points (-1 after a degenerate
+ *               stop)
+ *   cand_out    [cand_cap] int64 device: the candidates in list order
+ *   n_cand_out  host int64: the number of candidates
+ *   weights_out [cand_cap] int64 device or NULL: their weights
+ *   labels_out  [N] int32 device or NULL: each point's nearest candidate
+ *               (position in cand_out)
+ *   d2_out      [N] FP32 device or NULL: D^2 after the rounds
+ *   phi_out     [1] FP64 device or NULL: phi after the rounds
+ *   workspace   >= kpp_kmeans_par_workspace_size(N, d, cand_cap) bytes,
+ *               256-byte aligned
+ * Distances are the FP32 difference form.  The nearest new candidate of a
+ * point is searched on the tensor cores (the assignment of kpp_lloyd_step,
+ * same near-tie bound) and its distance then taken exactly; the recluster
+ * runs in one CTA.  The call synchronises `stream` once per round (the
+ * number of new candidates sizes the next launches) and at the end, and
+ * returns the device status: KPP_OK, KPP_ERR_DEGENERATE (fewer than K
+ * candidates carry weight), KPP_ERR_TIMEOUT, or KPP_ERR_CAPACITY (more than
+ * cand_cap candidates; nothing past the last whole round is written).
+ */
+KPP_API size_t kpp_kmeans_par_workspace_size(int64_t N, int32_t d, int64_t cand_cap);
+KPP_API kpp_status kpp_kmeans_par(const float *points, int64_t N, int32_t d, int32_t K,
+                                  double ell, int32_t rounds, uint64_t seed, uint64_t stream_id,
+                                  int64_t cand_cap, int64_t *idx_out, int64_t *cand_out,
+                                  int64_t *n_cand_out, int64_t *weights_out, int32_t *labels_out,
+                                  float *d2_out, double *phi_out, void *workspace,
+                                  size_t workspace_bytes, kpp_stream_t stream);
 
 /*
  * Seeding for callers that cannot allocate device memory.  (The paper has

@@ -28,7 +28,7 @@ from . import build as _build
 F32, BF16, FP8_E4M3 = 0, 1, 2
 FORM_AUTO, FORM_STREAMED, FORM_PERSISTENT, FORM_RECOMPUTE = 0, 1, 2, 3
 (OK, ERR_INVALID_ARG, ERR_CUDA, ERR_LAUNCH, ERR_TIMEOUT, ERR_DEGENERATE,
- ERR_WORKSPACE, ERR_UNSUPPORTED) = range(8)
+ ERR_WORKSPACE, ERR_UNSUPPORTED, ERR_CAPACITY) = range(9)
 
 _DTYPE_NAMES = {"f32": F32, "fp32": F32, "float32": F32, "bf16": BF16, "bfloat16": BF16,
                 "fp8": FP8_E4M3, "e4m3": FP8_E4M3, "fp8_e4m3": FP8_E4M3}
@@ -132,6 +132,11 @@ def load_library(build_if_stale: bool = True):
         lib.kpp_lloyd_step.restype = ctypes.c_int
         lib.kpp_lloyd_assign.argtypes = [P, I64, I32, I32, P, P, ctypes.c_size_t, P]
         lib.kpp_lloyd_assign.restype = ctypes.c_int
+        lib.kpp_kmeans_par_workspace_size.argtypes = [I64, I32, I64]
+        lib.kpp_kmeans_par_workspace_size.restype = ctypes.c_size_t
+        lib.kpp_kmeans_par.argtypes = [P, I64, I32, I32, ctypes.c_double, I32, U64, U64, I64, P, P,
+                                       P, P, P, P, P, P, ctypes.c_size_t, P]
+        lib.kpp_kmeans_par.restype = ctypes.c_int
         _lib = lib
         return lib
 
@@ -252,6 +257,19 @@ def kpp_lloyd_step(points, N, d, centres, K, labels_out, d2_out, centres_out, co
     return load_library().kpp_lloyd_step(points, N, d, centres, K, labels_out, d2_out,
                                          centres_out, counts_out, phi_out, workspace,
                                          workspace_bytes, stream)
+
+
+def kpp_kmeans_par_workspace_size(N, d, cand_cap) -> int:
+    return load_library().kpp_kmeans_par_workspace_size(N, d, cand_cap)
+
+
+def kpp_kmeans_par(points, N, d, K, ell, rounds, seed, stream_id, cand_cap, idx_out, cand_out,
+                   n_cand_out, weights_out, labels_out, d2_out, phi_out, workspace,
+                   workspace_bytes, stream) -> int:
+    """``n_cand_out``: address of a host int64 (e.g. ``ctypes.addressof``)."""
+    return load_library().kpp_kmeans_par(points, N, d, K, ell, rounds, seed, stream_id, cand_cap,
+                                         idx_out, cand_out, n_cand_out, weights_out, labels_out,
+                                         d2_out, phi_out, workspace, workspace_bytes, stream)
 
 
 # ---------------------------------------------------------------------------
@@ -420,6 +438,59 @@ class Lloyd:
                 if st != OK:
                     raise KppError(st, "kpp_lloyd_step (device)")
         return labels, d2, out, counts, phi
+
+
+def kmeans_par_cap(ell: float, rounds: int) -> int:
+    """Default room for the candidates: c_0 plus, per round, the expected
+    ell draws and 8 standard deviations (a round draws a sum of Bernoullis
+    with mean <= ell, so its variance is <= ell) and a small margin."""
+    import math
+
+    e = max(float(ell), 0.0) if math.isfinite(ell) else 0.0
+    return 1 + max(int(rounds), 0) * int(math.ceil(e + 8.0 * math.sqrt(e) + 16.0))
+
+
+def kmeans_par(points, K: int, seed: int, stream_id: int = 0, *, ell=None, rounds: int = 5,
+               cand_cap=None, workspace=None):
+    """k-means|| on FP32 CUDA points [N, d] through ``kpp_kmeans_par``
+    (``ell`` defaults to 2K).  Returns a dict: ``idx`` int64 [K] (the chosen
+    points), ``cand`` int64 [n] (the candidates in list order), ``weights``
+    int64 [n], ``labels`` int32 [N] (nearest candidate position), ``d2``
+    float32 [N] and ``phi`` float64 [1] after the rounds, ``status``.  A
+    degenerate stop (fewer than K weighted candidates) is reported in
+    ``status`` with -1 in ``idx``; other errors raise ``KppError``."""
+    import torch
+
+    if not points.is_cuda or points.dtype != torch.float32 or points.dim() != 2:
+        raise ValueError("points must be a 2-D float32 CUDA tensor")
+    x = points.contiguous()
+    N, d = x.shape
+    ell = float(2 * K if ell is None else ell)
+    cap = int(cand_cap if cand_cap is not None else min(N, kmeans_par_cap(ell, rounds)))
+    dev = x.device
+    with torch.cuda.device(dev):
+        if workspace is None:
+            n = kpp_kmeans_par_workspace_size(N, d, cap)
+            if n == 0:
+                raise KppError(ERR_INVALID_ARG, "kpp_kmeans_par_workspace_size")
+            workspace = torch.empty(n, dtype=torch.uint8, device=dev)
+        idx = torch.empty(K, dtype=torch.int64, device=dev)
+        cand = torch.empty(max(cap, 1), dtype=torch.int64, device=dev)
+        w = torch.empty(max(cap, 1), dtype=torch.int64, device=dev)
+        labels = torch.empty(N, dtype=torch.int32, device=dev)
+        d2 = torch.empty(N, dtype=torch.float32, device=dev)
+        phi = torch.empty(1, dtype=torch.float64, device=dev)
+        nc = ctypes.c_int64(0)
+        st = kpp_kmeans_par(x.data_ptr(), N, d, int(K), ell, int(rounds), int(seed),
+                            int(stream_id), cap, idx.data_ptr(), cand.data_ptr(),
+                            ctypes.addressof(nc), w.data_ptr(), labels.data_ptr(), d2.data_ptr(),
+                            phi.data_ptr(), workspace.data_ptr(), workspace.numel(),
+                            _stream_handle(dev))
+    if st not in (OK, ERR_DEGENERATE):
+        raise KppError(st, "kpp_kmeans_par")
+    n = nc.value
+    return {"idx": idx, "cand": cand[:n], "weights": w[:n], "labels": labels, "d2": d2,
+            "phi": phi, "status": st}
 
 
 def seed_host(points_host, K: int, seed: int, stream_id: int = 0, *, dtype=None,

@@ -361,6 +361,8 @@ const char *kpp_status_string(kpp_status s)
         return "workspace missing, misaligned or too small";
     case KPP_ERR_UNSUPPORTED:
         return "unsupported option combination";
+    case KPP_ERR_CAPACITY:
+        return "more k-means|| candidates than the room given";
     }
     return "unknown status";
 }

@@ -61,11 +61,13 @@ struct Problem {
 // ---------------------------------------------------------------------------
 // Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two 64x64
 // multiplies with the published multipliers, key bumped by the published Weyl
-// constants between rounds.  u_m takes the top 53 bits of output word 0.
+// constants between rounds.  A uniform takes the top 53 bits of output word
+// 0; the k-means++ draw u_m uses the counter {m, 0, 0, 0}.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ double philox_uniform(uint64_t seed, uint64_t stream, uint64_t m)
+__device__ __forceinline__ double philox_uniform_ctr(uint64_t seed, uint64_t stream, uint64_t c0,
+                                                     uint64_t c1, uint64_t c2, uint64_t c3)
 {
-    uint64_t x0 = m, x1 = 0, x2 = 0, x3 = 0;
+    uint64_t x0 = c0, x1 = c1, x2 = c2, x3 = c3;
     uint64_t k0 = seed, k1 = stream;
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
@@ -82,6 +84,11 @@ __device__ __forceinline__ double philox_uniform(uint64_t seed, uint64_t stream,
         k1 += 0xBB67AE8584CAA73Bull;
     }
     return (double)(x0 >> 11) * 0x1.0p-53;
+}
+
+__device__ __forceinline__ double philox_uniform(uint64_t seed, uint64_t stream, uint64_t m)
+{
+    return philox_uniform_ctr(seed, stream, m, 0, 0, 0);
 }
 
 // First seed: min(floor(u_0 * N), N - 1), or the forced index.

@@ -33,7 +33,7 @@ def test_header_declares_the_boundary():
                      "kpp_seed_batched", "kpp_batch_workspace_size", "kpp_seed_noalloc",
                      "kpp_tune", "kpp_tune_workspace_size", "kpp_tune_clear",
                      "kpp_lloyd_workspace_size", "kpp_lloyd_prepare", "kpp_lloyd_step",
-                     "kpp_lloyd_assign"]:
+                     "kpp_lloyd_assign", "kpp_kmeans_par_workspace_size", "kpp_kmeans_par"]:
         assert required in names
 
 
@@ -55,7 +55,7 @@ def test_host_only_entry_points(lib):
     import paper_1908_02136_gb300 as kpp
 
     assert kpp.kpp_version() >= 100
-    for code in range(8):
+    for code in range(9):
         s = kpp.kpp_status_string(code)
         assert isinstance(s, str) and s and s != "unknown status"
     assert kpp.kpp_status_string(99) == "unknown status"
@@ -72,6 +72,13 @@ def test_invalid_arguments_fail_synchronously(lib):
     assert kpp.kpp_workspace_size(10, 0, 1, 0) == 0
     assert kpp.kpp_workspace_size(10, 2, 1, 7) == 0
     assert kpp.kpp_quantize(None, 4, 4, kpp.BF16, None, None, None) == kpp.ERR_INVALID_ARG
+    assert kpp.kpp_kmeans_par_workspace_size(10, 129, 5) == 0
+    assert kpp.kpp_kmeans_par_workspace_size(10, 4, 0) == 0
+    import ctypes
+
+    nc = ctypes.c_int64(-1)
+    assert kpp.kpp_kmeans_par(None, 10, 4, 2, 4.0, 2, 1, 0, 5, None, None, ctypes.addressof(nc),
+                              None, None, None, None, None, 0, None) == kpp.ERR_INVALID_ARG
 
 
 def test_ctypes_structs_match_the_header(tmp_path):
