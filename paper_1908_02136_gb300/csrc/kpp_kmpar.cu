@@ -21,6 +21,7 @@
 //
 // Per-CTA sums are FP64 over a fixed partition of the points and combined in
 // CTA order, so a run is deterministic.
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include <cstring>
@@ -36,7 +37,7 @@ constexpr int kGrid = 1024;        // their CTAs; each owns a contiguous range o
 constexpr int kChunk = 4096;       // candidates per tensor-core assignment (its K limit)
 constexpr int kMaxD = 128;
 constexpr int kRecThreads = 1024;  // recluster CTA
-constexpr int kRowsInFlight = 4;   // rows a warp loads before reducing
+constexpr int kRowsInFlight = 8;   // rows a warp loads before reducing (<= 32)
 constexpr size_t kAlign = 256;
 
 size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
@@ -51,7 +52,8 @@ struct Layout {
     int64_t range; // points per CTA
     int64_t cap;   // candidates the workspace holds
     size_t off_scal, off_d2, off_lab, off_tmp, off_flags, off_bcnt, off_boff, off_part, off_cbuf,
-        off_w, off_rd2, off_rval, off_lloyd, lloyd_bytes, bytes;
+        off_w, off_ct, off_lloyd, lloyd_bytes, bytes;
+    int64_t ldc; // leading dimension of the feature-major candidate copy
 };
 
 bool shape_ok(int64_t N, int32_t d, int64_t cap)
@@ -87,10 +89,9 @@ Layout layout(int64_t N, int32_t d, int64_t cand_cap)
     off += (size_t)L.cap * d * 4;
     L.off_w = off = round_up(off, kAlign);
     off += (size_t)L.cap * 8;
-    L.off_rd2 = off = round_up(off, kAlign);
-    off += (size_t)L.cap * 4;
-    L.off_rval = off = round_up(off, kAlign);
-    off += (size_t)L.cap * 8;
+    L.ldc = (L.cap + 31) / 32 * 32;
+    L.off_ct = off = round_up(off, kAlign);
+    off += (size_t)L.ldc * d * 4;
     L.off_lloyd = off = round_up(off, kAlign);
     L.lloyd_bytes = kpp_lloyd_workspace_size(N, d, lloyd_k(N));
     off += L.lloyd_bytes;
@@ -130,17 +131,18 @@ __device__ __forceinline__ void load_row(const float *x, int64_t row, int d, int
     }
 }
 
-// The CTA's FP64 sum of per-warp FP64 partials, combined in warp order.
-__device__ __forceinline__ double cta_sum_ordered(double v, double *sh)
+// The CTA's sum of per-warp pair partials, combined in warp order (valid in
+// thread 0).  Every lane of a warp holds the same partial.
+__device__ __forceinline__ Pair cta_sum_ordered(const Pair &v, Pair *sh)
 {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (lane == 0)
         sh[warp] = v;
     __syncthreads();
-    double s = 0.0;
+    Pair s{};
     if (threadIdx.x == 0)
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
-            s += sh[w];
+            s.add(sh[w]);
     return s;
 }
 
@@ -151,10 +153,10 @@ __global__ void __launch_bounds__(kThreads) kmpar_init_kernel(const float *x, in
                                                               int64_t range, uint64_t seed,
                                                               uint64_t stream, float *D2,
                                                               int32_t *lab, int64_t *cand,
-                                                              float *cbuf, double *part)
+                                                              float *cbuf, Pair *part)
 {
     __shared__ float c[kMaxD];
-    __shared__ double sh[kThreads / 32];
+    __shared__ Pair sh[kThreads / 32];
     const double u0 = philox_uniform(seed, stream, 0);
     int64_t c0 = (int64_t)floor(u0 * (double)N);
     c0 = c0 < N - 1 ? c0 : N - 1;
@@ -169,39 +171,45 @@ __global__ void __launch_bounds__(kThreads) kmpar_init_kernel(const float *x, in
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     const int64_t lo = blockIdx.x * range, hi = lo + range < N ? lo + range : N;
-    double acc = 0.0;
+    // a warp takes kRowsInFlight rows at a time; lane q keeps row q's
+    // result, so the D^2 and label stores of a batch are one coalesced store
+    Pair acc{};
     for (int64_t r0 = lo + (int64_t)warp * kRowsInFlight; r0 < hi; r0 += (int64_t)nw * kRowsInFlight) {
         float xv[kRowsInFlight][4];
 #pragma unroll
         for (int q = 0; q < kRowsInFlight; ++q)
             load_row(x, r0 + q, d, lane, r0 + q < hi, xv[q]);
+        float mine = 0.f;
 #pragma unroll
         for (int q = 0; q < kRowsInFlight; ++q) {
-            const int64_t row = r0 + q;
-            const float s = lane_sq(xv[q], c, d, lane);
-            if (row < hi) {
-                if (lane == 0) {
-                    D2[row] = s;
-                    lab[row] = 0;
-                }
-                acc += (double)s;
-            }
+            const float sq = lane_sq(xv[q], c, d, lane);
+            mine = lane == q ? sq : mine;
+        }
+        const int64_t row = r0 + lane;
+        if (lane < kRowsInFlight && row < hi) {
+            D2[row] = mine;
+            lab[row] = 0;
+            acc.add(mine);
         }
     }
-    const double t = cta_sum_ordered(acc, sh);
+    acc = warp_pair_sum(acc);
+    const Pair t = cta_sum_ordered(acc, sh);
     if (threadIdx.x == 0)
         part[blockIdx.x] = t;
 }
 
-// phi = sum of the CTA partials in CTA order
-__global__ void kmpar_phi_kernel(const double *part, int n, Scalars *sc)
+// phi = sum of the CTA partials (one warp: lane l adds partials l*per ..
+// in order, then a butterfly), FP64 only for the final hi + lo.
+__global__ void kmpar_phi_kernel(const Pair *part, int n, Scalars *sc)
 {
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
-        double s = 0.0;
-        for (int b = 0; b < n; ++b)
-            s += part[b];
-        sc->phi = s;
-    }
+    const int lane = threadIdx.x & 31;
+    const int per = (n + 31) / 32;
+    Pair s{};
+    for (int b = lane * per; b < n && b < (lane + 1) * per; ++b)
+        s.add(part[b]);
+    s = warp_pair_sum(s);
+    if (lane == 0)
+        sc->phi = s.value();
 }
 
 // ---------------------------------------------------------------------------
@@ -213,12 +221,27 @@ __global__ void __launch_bounds__(kThreads)
 {
     __shared__ int wc[kThreads / 32];
     const double phi = sc->phi;
+    // FP32 estimate of p = ell D^2 / phi, within a few ulps; the FP64
+    // decision is taken only when u is within 2^-20 (relative, plus 2^-100
+    // absolute for tiny p) of it -- GB300's FP64 divide is slow.
+    const float scale = phi > 0.0 ? (float)(ell / phi) : 0.f;
+    const bool fast = phi > 0.0 && scale < 1e30f && scale > 1e-30f;
     const int64_t lo = blockIdx.x * range, hi = lo + range < N ? lo + range : N;
     int n = 0;
     for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-        const double p = phi > 0.0 ? ell * (double)D2[i] / phi : 0.0;
-        const double u = philox_uniform_ctr(seed, stream, (uint64_t)i, (uint64_t)r + 1, 0, 0);
-        const uint8_t f = u < p ? 1 : 0;
+        const float d2 = D2[i];
+        uint8_t f = 0;
+        if (phi > 0.0 && d2 > 0.f) {
+            const double u = philox_uniform_ctr(seed, stream, (uint64_t)i, (uint64_t)r + 1, 0, 0);
+            const float pf = scale * d2;
+            const float uf = (float)u;
+            if (fast && pf < 1e30f && uf < pf * (1.f - 0x1.0p-20f) - 0x1.0p-100f)
+                f = 1;
+            else if (fast && pf < 1e30f && uf > pf * (1.f + 0x1.0p-20f) + 0x1.0p-100f)
+                f = 0;
+            else
+                f = u < ell * (double)d2 / phi ? 1 : 0;
+        }
         flags[i] = f;
         n += f;
     }
@@ -318,43 +341,45 @@ __global__ void __launch_bounds__(kThreads)
 __global__ void __launch_bounds__(kThreads)
     kmpar_min_update_kernel(const float *x, int64_t N, int d, int64_t range, const float *cbuf,
                             int64_t base, int32_t n, const int32_t *pick, float *D2, int32_t *lab,
-                            double *part)
+                            Pair *part)
 {
-    __shared__ double sh[kThreads / 32];
+    __shared__ Pair sh[kThreads / 32];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     const int64_t lo = blockIdx.x * range, hi = lo + range < N ? lo + range : N;
-    double acc = 0.0;
+    Pair acc{};
     for (int64_t r0 = lo + (int64_t)warp * kRowsInFlight; r0 < hi; r0 += (int64_t)nw * kRowsInFlight) {
+        // lane q < kRowsInFlight loads row q's label, D^2 and nearest so far
+        const int64_t row = r0 + lane;
+        const bool own = lane < kRowsInFlight && row < hi;
+        // (a label outside the chunk -- only possible if the assignment gave
+        // up on a timeout, which the host reports -- reads position base)
+        int32_t pk = own ? pick[row] : 0;
+        pk = (unsigned)pk < (unsigned)n ? pk : 0;
+        float cur = own ? D2[row] : 0.f;
+        const int32_t l = own ? lab[row] : 0;
         float xv[kRowsInFlight][4];
-        int64_t pos[kRowsInFlight];
+#pragma unroll
+        for (int q = 0; q < kRowsInFlight; ++q)
+            load_row(x, r0 + q, d, lane, r0 + q < hi, xv[q]);
+        float mine = 0.f;
 #pragma unroll
         for (int q = 0; q < kRowsInFlight; ++q) {
-            const bool ok = r0 + q < hi;
-            load_row(x, r0 + q, d, lane, ok, xv[q]);
-            // (a label outside the chunk -- only possible if the assignment
-            // gave up on a timeout, which the host reports -- reads row 0)
-            const int32_t pk = ok ? pick[r0 + q] : 0;
-            pos[q] = base + ((unsigned)pk < (unsigned)n ? pk : 0);
+            const int32_t pq = __shfl_sync(0xffffffffu, pk, q);
+            const float sq = lane_sq(xv[q], cbuf + (base + pq) * d, d, lane);
+            mine = lane == q ? sq : mine;
         }
-#pragma unroll
-        for (int q = 0; q < kRowsInFlight; ++q) {
-            const int64_t row = r0 + q;
-            const float s = lane_sq(xv[q], cbuf + pos[q] * d, d, lane);
-            if (row < hi) {
-                float cur = D2[row];
-                const int32_t l = lab[row];
-                if (s < cur || (s == cur && pos[q] < l)) {
-                    cur = s;
-                    if (lane == 0) {
-                        D2[row] = s;
-                        lab[row] = (int32_t)pos[q];
-                    }
-                }
-                acc += (double)cur;
+        if (own) {
+            const int64_t pos = base + pk;
+            if (mine < cur || (mine == cur && pos < l)) {
+                cur = mine;
+                D2[row] = mine;
+                lab[row] = (int32_t)pos;
             }
+            acc.add(cur);
         }
     }
-    const double t = cta_sum_ordered(acc, sh);
+    acc = warp_pair_sum(acc);
+    const Pair t = cta_sum_ordered(acc, sh);
     if (threadIdx.x == 0)
         part[blockIdx.x] = t;
 }
@@ -375,114 +400,316 @@ __global__ void kmpar_weights_out_kernel(const unsigned long long *w, int64_t n,
 }
 
 // ---------------------------------------------------------------------------
-// Step 4: weighted k-means++ over the nc candidates, one CTA.  Thread t owns
-// candidates [t S, t S + S); per centre m it updates their D^2 to the last
-// centre (FP32 difference form) and values w D^2 (FP64), sums them in order,
-// and a block scan gives every thread the FP64 prefix before its run.  The
-// pick is the earliest candidate whose running prefix exceeds t = v_m T (the
-// last candidate with a positive value if rounding leaves none).
+// Step 4: weighted k-means++ over the nc candidates, on one thread-block
+// cluster (up to 16 CTAs, one per SM, so the per-step L2 reads of the
+// candidates' coordinates spread over that many SMs).  CTA r owns the
+// contiguous slice [r S, r S + S) of the candidate list, thread t of it the
+// contiguous run [t R, t R + R) of the slice; D^2 and the weights of the
+// slice stay in shared memory, the coordinates are read feature-major (cT,
+// coalesced across a warp).  Per centre m:
+//   1. every thread updates D^2 of its run to the last centre (FP32
+//      difference form, features in order), forms v = w D^2 as an FP32
+//      two-sum pair (w split into two floats, products with their exact
+//      FMA error terms) and sums its run in order;
+//   2. a CTA scan gives the slice total, which every CTA reads from every
+//      other CTA's shared memory after a cluster barrier; all CTAs prefix
+//      the totals in rank order the same way, so they agree on T, on the
+//      threshold t = v_m T and on the CTA whose prefix first exceeds t;
+//   3. that CTA walks its runs from its exclusive prefix and takes the first
+//      candidate whose running prefix exceeds t (decided in FP32 pairs, or
+//      exactly in FP64 when within 2^-40 t of it); if rounding leaves no
+//      crossing it takes its last candidate with a positive value, and if no
+//      CTA's prefix exceeds t the last CTA with a positive total does the
+//      same (the clamp of the inverse CDF);
+//   4. after a second cluster barrier every CTA reads the pick from that
+//      CTA's shared memory and loads the new centre.
+// T = 0 at a draw (fewer than K candidates carry weight) is a degenerate
+// stop: the remaining indices are -1.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ double warp_incl_scan(double v)
+constexpr int kRecMaxCluster = 16;
+constexpr int kRecPerCta = 512; // target candidates per CTA
+
+struct RecArgs {
+    const float *cT; // [d][ldc] candidate coordinates, feature-major
+    int64_t ldc;
+    const float *cbuf; // [nc][d]
+    int64_t nc;
+    int32_t d;
+    int32_t K;
+    int64_t slice;  // candidates per CTA
+    int64_t run;    // candidates per thread
+    int32_t staged; // the slice's coordinates are copied to shared memory
+    const unsigned long long *w;
+    uint64_t seed, stream;
+    const int64_t *cand;
+    int64_t *idx_out;
+    Control *ctl;
+};
+
+// w * r as a pair: w = whi + wlo (two floats, exact for w < 2^48), each
+// product with its exact FMA error term.
+__device__ __forceinline__ Pair weighted(float whi, float wlo, float r)
 {
-    const int lane = threadIdx.x & 31;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const double y = __shfl_up_sync(0xffffffffu, v, o);
-        if (lane >= o)
-            v += y;
-    }
+    const float p1 = __fmul_rn(whi, r);
+    const float e1 = __fmaf_rn(whi, r, -p1);
+    const float p2 = __fmul_rn(wlo, r);
+    const float e2 = __fmaf_rn(wlo, r, -p2);
+    Pair v{p1, e1};
+    v.add(p2);
+    v.lo = __fadd_rn(v.lo, e2);
     return v;
 }
 
-__global__ void __launch_bounds__(kRecThreads, 1)
-    kmpar_recluster_kernel(const float *cbuf, int64_t nc, int d, const unsigned long long *w,
-                           int K, uint64_t seed, uint64_t stream, const int64_t *cand, float *rd2,
-                           double *rval, int64_t *idx_out, Control *ctl)
+__global__ void __launch_bounds__(kRecThreads, 1) kmpar_recluster_kernel(RecArgs a)
 {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    const int C = (int)cl.num_blocks();
+    // [slice] D^2, [slice] w hi, [slice] w lo, then (staged) [d][slice]
+    // coordinates
+    extern __shared__ float rsm[];
+    float *s_rd2 = rsm, *s_whi = rsm + a.slice, *s_wlo = rsm + 2 * a.slice;
+    float *s_x = rsm + 3 * a.slice;
     __shared__ float cen[kMaxD];
-    __shared__ double wsum[kRecThreads / 32], wex[kRecThreads / 32];
-    __shared__ double s_T;
+    __shared__ Pair s_wx[kRecThreads / 32]; // warp totals, then their exclusive prefix
+    __shared__ Pair s_cta;                  // this CTA's total (read by the cluster)
+    __shared__ Pair s_E;                    // prefix before this CTA
+    __shared__ Thresh s_th;
+    __shared__ int s_des, s_clamp;
     __shared__ unsigned long long s_pick;
-    __shared__ long long s_last;
-    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    const int64_t S = (nc + kRecThreads - 1) / kRecThreads;
-    const int64_t c_lo = (int64_t)t * S < nc ? (int64_t)t * S : nc;
-    const int64_t c_hi = c_lo + S < nc ? c_lo + S : nc;
-    for (int m = 0; m < K; ++m) {
-        // this thread's run: D^2 to the last centre, values, their sum in order
-        double seg = 0.0;
+    __shared__ long long s_last, s_res;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5, nw = blockDim.x >> 5;
+    const int64_t lo = (int64_t)rank * a.slice;
+    const int64_t hi = lo + a.slice < a.nc ? lo + a.slice : a.nc;
+    const int64_t r0 = lo + (int64_t)t * a.run < hi ? lo + (int64_t)t * a.run : hi;
+    const int64_t r1 = r0 + a.run < hi ? r0 + a.run : hi;
+    for (int64_t c = lo + t; c < hi; c += blockDim.x) {
+        const unsigned long long wv = a.w[c];
+        const float wh = __ull2float_rn(wv);
+        s_whi[c - lo] = wh;
+        s_wlo[c - lo] = (float)((long long)wv - (long long)wh);
+    }
+    if (a.staged)
+        for (int j = 0; j < a.d; ++j)
+            for (int64_t c = lo + t; c < hi; c += blockDim.x)
+                s_x[(int64_t)j * a.slice + (c - lo)] = a.cT[(int64_t)j * a.ldc + c];
+    __syncthreads();
+    for (int m = 0; m < a.K; ++m) {
+        // 1. this thread's run
+        Pair seg{};
         long long last = -1;
-        for (int64_t c = c_lo; c < c_hi; ++c) {
-            double v;
+        for (int64_t c = r0; c < r1; ++c) {
+            const int li = (int)(c - lo);
+            Pair v;
             if (m == 0) {
-                rd2[c] = __int_as_float(0x7f800000);
-                v = (double)w[c];
+                s_rd2[li] = __int_as_float(0x7f800000);
+                v = Pair{s_whi[li], s_wlo[li]};
             } else {
                 float s = 0.f;
-                for (int j = 0; j < d; ++j) {
-                    const float q = cbuf[c * d + j] - cen[j];
-                    s = fmaf(q, q, s);
+                if (a.staged) {
+#pragma unroll 8
+                    for (int j = 0; j < a.d; ++j) {
+                        const float q = s_x[(int64_t)j * a.slice + li] - cen[j];
+                        s = fmaf(q, q, s);
+                    }
+                } else {
+#pragma unroll 8
+                    for (int j = 0; j < a.d; ++j) {
+                        const float q = __ldg(a.cT + (int64_t)j * a.ldc + c) - cen[j];
+                        s = fmaf(q, q, s);
+                    }
                 }
-                float cur = rd2[c];
-                if (s < cur) {
-                    cur = s;
-                    rd2[c] = s;
+                float r = s_rd2[li];
+                if (s < r) {
+                    r = s;
+                    s_rd2[li] = s;
                 }
-                v = (double)w[c] * (double)cur;
+                v = weighted(s_whi[li], s_wlo[li], r);
             }
-            rval[c] = v;
-            seg += v;
-            if (v > 0.0)
-                last = (long long)c;
+            seg.add(v);
+            if (v.hi > 0.f)
+                last = c;
         }
-        // block scan of the run sums: in-warp, then over the warp totals
-        const double inc = warp_incl_scan(seg);
-        double ex = __shfl_up_sync(0xffffffffu, inc, 1);
-        if (lane == 0)
-            ex = 0.0;
+        // 2. CTA scan, then the cluster's totals
+        Pair ex;
+        const Pair inc = warp_pair_scan(seg, ex);
         if (lane == 31)
-            wsum[warp] = inc;
+            s_wx[warp] = inc;
         __syncthreads();
         if (warp == 0) {
-            const double wi = warp_incl_scan(wsum[lane]);
-            double we = __shfl_up_sync(0xffffffffu, wi, 1);
-            wex[lane] = lane == 0 ? 0.0 : we;
+            const Pair wv = lane < nw ? s_wx[lane] : Pair{};
+            Pair wex;
+            const Pair wi = warp_pair_scan(wv, wex);
+            if (lane < nw)
+                s_wx[lane] = wex;
             if (lane == 31)
-                s_T = wi;
+                s_cta = wi;
             if (lane == 0) {
                 s_pick = ~0ull;
                 s_last = -1;
             }
         }
-        __syncthreads();
-        const double T = s_T;
-        if (!(T > 0.0)) {
-            // fewer than K candidates carry weight: degenerate stop
-            if (t == 0)
-                atomicCAS(&ctl->status, KPP_OK, KPP_ERR_DEGENERATE);
-            for (int k = m + t; k < K; k += blockDim.x)
-                idx_out[k] = -1;
-            return;
-        }
-        const double th = philox_uniform_ctr(seed, stream, (uint64_t)m, 0, 1, 0) * T;
-        double P = wex[warp] + ex;
-        for (int64_t c = c_lo; c < c_hi; ++c) {
-            P += rval[c];
-            if (P > th) {
-                atomicMin(&s_pick, (unsigned long long)c);
-                break;
+        cl.sync(); // every CTA's total is published
+        if (warp == 0) {
+            const Pair tv = lane < C ? *cl.map_shared_rank(&s_cta, (unsigned)lane) : Pair{};
+            Pair tex;
+            const Pair ti = warp_pair_scan(tv, tex);
+            const Pair T = shfl_pair(ti, 31);
+            Thresh th = thresh_for_u(philox_uniform_ctr(a.seed, a.stream, (uint64_t)m, 0, 1, 0));
+            thresh_set_total(th, T);
+            const unsigned cm = __ballot_sync(0xffffffffu, lane < C && th.gt(ti));
+            const unsigned pm = __ballot_sync(0xffffffffu, lane < C && tv.hi > 0.f);
+            if (lane == rank)
+                s_E = tex;
+            if (lane == 0) {
+                s_th = th;
+                s_des = cm ? __ffs(cm) - 1 : (pm ? 31 - __clz(pm) : -1);
+                s_clamp = cm ? 0 : 1;
             }
         }
-        if (last >= 0)
-            atomicMax(&s_last, last);
         __syncthreads();
-        const int64_t pick = s_pick != ~0ull ? (int64_t)s_pick : (int64_t)s_last;
-        if (t < d)
-            cen[t] = cbuf[pick * d + t];
-        if (t == 0)
-            idx_out[m] = cand[pick];
+        const Thresh th = s_th;
+        const int des = s_des;
+        if (!(th.T.hi > 0.f) || des < 0) {
+            // degenerate stop
+            if (rank == 0) {
+                if (t == 0)
+                    atomicCAS(&a.ctl->status, KPP_OK, KPP_ERR_DEGENERATE);
+                for (int k = m + t; k < a.K; k += blockDim.x)
+                    a.idx_out[k] = -1;
+            }
+            cl.sync();
+            return;
+        }
+        // 3. the designated CTA finds the crossing
+        if (rank == des) {
+            if (!s_clamp) {
+                Pair P = s_E;
+                P.add(s_wx[warp]);
+                P.add(ex);
+                for (int64_t c = r0; c < r1; ++c) {
+                    const int li = (int)(c - lo);
+                    const Pair v = m == 0 ? Pair{s_whi[li], s_wlo[li]}
+                                          : weighted(s_whi[li], s_wlo[li], s_rd2[li]);
+                    P.add(v);
+                    if (v.hi > 0.f && th.gt(P)) {
+                        atomicMin(&s_pick, (unsigned long long)c);
+                        break;
+                    }
+                }
+            }
+            if (last >= 0)
+                atomicMax(&s_last, last);
+            __syncthreads();
+            if (t == 0)
+                s_res = s_pick != ~0ull ? (long long)s_pick : s_last;
+        }
+        cl.sync(); // the pick is published
+        // 4. every CTA takes the new centre
+        if (t < a.d) {
+            const long long pick = *cl.map_shared_rank(&s_res, (unsigned)des);
+            for (int j = t; j < a.d; j += blockDim.x)
+                cen[j] = a.cbuf[pick * a.d + j];
+            if (t == 0 && rank == 0)
+                a.idx_out[m] = a.cand[pick];
+        }
         __syncthreads();
     }
+    cl.sync(); // no CTA leaves while another may still read its shared memory
+}
+
+// cT[j][c] = cbuf[c][j]
+__global__ void kmpar_transpose_kernel(const float *cbuf, int64_t nc, int d, int64_t ldc, float *cT)
+{
+    const int64_t n = nc * d;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c = e / d;
+        const int j = (int)(e - c * d);
+        cT[(int64_t)j * ldc + c] = cbuf[e];
+    }
+}
+
+// Cluster shape of the recluster: C CTAs of T threads, S candidates per CTA,
+// R per thread; false if the candidates do not fit.
+struct RecShape {
+    int C, T;
+    int64_t S, R;
+    bool staged;
+    size_t smem;
+};
+
+bool rec_shape(int64_t nc, int d, int max_cluster, RecShape *out)
+{
+    RecShape r;
+    r.C = (int)((nc + kRecPerCta - 1) / kRecPerCta);
+    r.C = r.C < 1 ? 1 : (r.C > max_cluster ? max_cluster : r.C);
+    r.S = (nc + r.C - 1) / r.C;
+    r.T = (int)((r.S + 31) / 32 * 32);
+    r.T = r.T > kRecThreads ? kRecThreads : r.T;
+    r.R = (r.S + r.T - 1) / r.T;
+    r.staged = (size_t)r.S * (12 + 4 * (size_t)d) <= 200 * 1024;
+    r.smem = (size_t)r.S * (r.staged ? 12 + 4 * (size_t)d : 12);
+    *out = r;
+    return r.smem <= 200 * 1024;
+}
+
+// Largest cluster (16 if the device schedules it, else 8) for this kernel.
+int rec_max_cluster()
+{
+    static int cached = 0;
+    if (cached)
+        return cached;
+    int best = 8;
+    if (cudaFuncSetAttribute(kmpar_recluster_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed,
+                             1) == cudaSuccess &&
+        cudaFuncSetAttribute(kmpar_recluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             200 * 1024) == cudaSuccess) {
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = kRecMaxCluster;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3(kRecMaxCluster);
+        cfg.blockDim = dim3(kRecThreads);
+        cfg.dynamicSmemBytes = 200 * 1024;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int n = 0;
+        if (cudaOccupancyMaxActiveClusters(&n, kmpar_recluster_kernel, &cfg) == cudaSuccess &&
+            n >= 1)
+            best = kRecMaxCluster;
+    }
+    cudaGetLastError();
+    cached = best;
+    return best;
+}
+
+cudaError_t rec_launch(const RecShape &r, const RecArgs &a, cudaStream_t s)
+{
+    cudaError_t e = cudaFuncSetAttribute(kmpar_recluster_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)r.smem);
+    if (e != cudaSuccess)
+        return e;
+    if (r.C > 8 && (e = cudaFuncSetAttribute(kmpar_recluster_kernel,
+                                             cudaFuncAttributeNonPortableClusterSizeAllowed, 1)) !=
+                       cudaSuccess)
+        return e;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)r.C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3((unsigned)r.C);
+    cfg.blockDim = dim3((unsigned)r.T);
+    cfg.dynamicSmemBytes = r.smem;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kmpar_recluster_kernel, a);
 }
 
 int sm_count()
@@ -536,11 +763,10 @@ kpp_status kpp_kmeans_par(const float *points, int64_t N, int32_t d, int32_t K, 
     uint8_t *flags = reinterpret_cast<uint8_t *>(ws + L.off_flags);
     long long *bcnt = reinterpret_cast<long long *>(ws + L.off_bcnt);
     long long *boff = reinterpret_cast<long long *>(ws + L.off_boff);
-    double *part = reinterpret_cast<double *>(ws + L.off_part);
+    Pair *part = reinterpret_cast<Pair *>(ws + L.off_part);
     float *cbuf = reinterpret_cast<float *>(ws + L.off_cbuf);
     auto *wts = reinterpret_cast<unsigned long long *>(ws + L.off_w);
-    float *rd2 = reinterpret_cast<float *>(ws + L.off_rd2);
-    double *rval = reinterpret_cast<double *>(ws + L.off_rval);
+    float *cT = reinterpret_cast<float *>(ws + L.off_ct);
     void *lws = ws + L.off_lloyd;
     const int kl = lloyd_k(N);
     auto launched = [] { return cudaGetLastError() == cudaSuccess; };
@@ -597,8 +823,29 @@ kpp_status kpp_kmeans_par(const float *points, int64_t N, int32_t d, int32_t K, 
     if (cudaMemsetAsync(wts, 0, (size_t)nc * 8, s) != cudaSuccess)
         return KPP_ERR_CUDA;
     kmpar_weights_kernel<<<kGrid, kThreads, 0, s>>>(lab, N, wts);
-    kmpar_recluster_kernel<<<1, kRecThreads, 0, s>>>(cbuf, nc, d, wts, K, seed, stream_id,
-                                                     cand_out, rd2, rval, idx_out, ctl);
+    RecShape rs;
+    if (!rec_shape(nc, d, rec_max_cluster(), &rs))
+        return KPP_ERR_UNSUPPORTED;
+    kmpar_transpose_kernel<<<(int)((nc * d + 255) / 256 < 4096 ? (nc * d + 255) / 256 : 4096), 256,
+                             0, s>>>(cbuf, nc, d, L.ldc, cT);
+    RecArgs ra;
+    ra.cT = cT;
+    ra.ldc = L.ldc;
+    ra.cbuf = cbuf;
+    ra.nc = nc;
+    ra.d = d;
+    ra.K = K;
+    ra.slice = rs.S;
+    ra.run = rs.R;
+    ra.staged = rs.staged ? 1 : 0;
+    ra.w = wts;
+    ra.seed = seed;
+    ra.stream = stream_id;
+    ra.cand = cand_out;
+    ra.idx_out = idx_out;
+    ra.ctl = ctl;
+    if (rec_launch(rs, ra, s) != cudaSuccess)
+        return KPP_ERR_LAUNCH;
     if (weights_out)
         kmpar_weights_out_kernel<<<(int)((nc + 255) / 256), 256, 0, s>>>(wts, nc, weights_out);
     if (!launched())

@@ -91,16 +91,25 @@ __device__ __forceinline__ void split_bf16(float v, __nv_bfloat16 &hi, __nv_bflo
     lo = __float2bfloat16_rn(v - __bfloat162float(hi));
 }
 
+// A thread per (row, group of 8 features): eight FP32 loads, one 16-byte
+// store per plane.  dp / 8 is 8 or 16, so the indexing is shifts and masks.
 __global__ void split_rows_kernel(const float *x, int64_t rows, int d, int dp, __nv_bfloat16 *hi,
                                   __nv_bfloat16 *lo)
 {
-    const int64_t n = rows * dp;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t r = e / dp;
-        const int j = (int)(e - r * dp);
-        const float v = j < d ? x[r * d + j] : 0.f;
-        split_bf16(v, hi[e], lo[e]);
+    const int sh = dp == 64 ? 3 : 4;
+    const int64_t n = rows << sh;
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n;
+         g += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = g >> sh;
+        const int j0 = (int)(g & ((1 << sh) - 1)) << 3;
+        __align__(16) __nv_bfloat16 h[8], l[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int j = j0 + u;
+            split_bf16(j < d ? x[r * d + j] : 0.f, h[u], l[u]);
+        }
+        *reinterpret_cast<uint4 *>(hi + r * dp + j0) = *reinterpret_cast<const uint4 *>(h);
+        *reinterpret_cast<uint4 *>(lo + r * dp + j0) = *reinterpret_cast<const uint4 *>(l);
     }
 }
 
@@ -685,7 +694,7 @@ kpp_status kpp_lloyd_assign(const float *centres, int64_t N, int32_t d, int32_t 
         return KPP_ERR_UNSUPPORTED;
     if (cudaMemsetAsync(ws, 0, sizeof(Control), s) != cudaSuccess)
         return KPP_ERR_CUDA;
-    split_rows_kernel<<<(K * L.dp + 255) / 256, 256, 0, s>>>(centres, K, d, L.dp, chi, clo);
+    split_rows_kernel<<<(K * L.dp / 8 + 255) / 256, 256, 0, s>>>(centres, K, d, L.dp, chi, clo);
     centre_norms_kernel<<<(K + 127) / 128, 128, 0, s>>>(centres, K, d, cn);
     const int64_t n_grp = ((N + kBM - 1) / kBM + kMT - 1) / kMT;
     const int grid = (int)(n_grp < sms ? n_grp : sms);
