@@ -38,6 +38,7 @@ UNIT = "N*K*d/s"
 DEFAULT_WORKLOAD = "gmm-N1e6-d32-K256"
 BATCH_WORKLOAD = "batch-512"
 LLOYD_PREFIX = "lloyd-"  # e.g. lloyd-gmm-N1e7-d64-K1024: one Lloyd iteration from the seeds
+KMPAR_PREFIX = "kmpar-"  # e.g. kmpar-gmm-N1e6-d32-K256: k-means|| (ell = 2K, 5 rounds)
 
 
 def parse():
@@ -67,6 +68,8 @@ def parse():
     ap.add_argument("--n-points", type=int, default=0,
                     help="a smaller instance of the workload's recipe (profiling)")
     ap.add_argument("--k-seeds", type=int, default=0)
+    ap.add_argument("--ell-mult", type=float, default=2.0, help="k-means||: ell = this x K")
+    ap.add_argument("--rounds", type=int, default=5, help="k-means||: oversampling rounds")
     return ap.parse_args()
 
 
@@ -548,6 +551,124 @@ def run_lloyd(args, rank, world, dev, pg, barrier):
         }), flush=True)
 
 
+def run_kmpar(args, rank, world, dev, pg, barrier):
+    """k-means|| (kpp_kmeans_par) on a seeding workload's points: each step
+    is one whole initialisation (c_0, the oversampling rounds, the weights,
+    the weighted k-means++ recluster).  Its dominant kernel on the large
+    workloads is the tensor-core nearest-candidate search, timed alone
+    (kpp_lloyd_assign at K = ell candidates) for the roofline."""
+    import ctypes
+
+    import torch
+
+    import paper_1908_02136_gb300 as kpp
+    from paper_1908_02136_gb300 import datagen, multi
+
+    wl = datagen.WORKLOADS[args.workload[len(KMPAR_PREFIX):]]
+    x = datagen.workload_points(wl, dev)
+    N, d, K = wl.N, wl.d, wl.K
+    ell, R = args.ell_mult * K, args.rounds
+    cap = min(N, kpp.kmeans_par_cap(ell, R))
+    stream = torch.cuda.Stream(dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    seed, sid = wl.draw_seed, multi.replica_stream(0, rank)
+    with torch.cuda.stream(stream):
+        ws = torch.empty(kpp.kpp_kmeans_par_workspace_size(N, d, cap), dtype=torch.uint8,
+                         device=dev)
+
+        def step():
+            return kpp.kmeans_par(x, K, seed, sid, ell=ell, rounds=R, cand_cap=cap, workspace=ws)
+
+        for _ in range(args.warmup):
+            flush.fill_(1)
+            r = step()
+        n_cand = int(r["cand"].numel())
+        torch.cuda.synchronize(dev)
+        barrier()
+        sampler = ClockSampler(int(str(dev).split(":")[-1]) if ":" in str(dev) else 0)
+        sampler.start()
+        time.sleep(0.3)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        for a_, b_ in ev:
+            flush.fill_(3)
+            a_.record(stream)
+            r = step()
+            b_.record(stream)
+        torch.cuda.synchronize(dev)
+        # the dominant kernel alone: nearest of ell candidates for every point
+        ke = min(N, 4096, int(round(ell)))
+        ll = kpp.Lloyd(x, ke)
+        C = x[r["cand"][:ke]].contiguous() if n_cand >= ke else x[:ke].contiguous()
+        lab = torch.empty(N, dtype=torch.int32, device=dev)
+        sh = ctypes.c_void_p(stream.cuda_stream)
+        aev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+        for a_, b_ in aev:
+            flush.fill_(3)
+            a_.record(stream)
+            st = kpp.kpp_lloyd_assign(C.data_ptr(), N, d, ke, lab.data_ptr(), ll.ws.data_ptr(),
+                                      ll.ws.numel(), sh)
+            b_.record(stream)
+            if st != kpp.OK:
+                raise kpp.KppError(st, "kpp_lloyd_assign")
+        torch.cuda.synchronize(dev)
+        clocks = sampler.stop()
+        barrier()
+        st = kpp.kpp_read_status(ll.ws.data_ptr(), sh)
+        if st != kpp.OK:
+            raise kpp.KppError(st, "kpp_lloyd_assign (device)")
+    step_ms = [a_.elapsed_time(b_) for a_, b_ in ev]
+    a_ms = statistics.fmean(a_.elapsed_time(b_) for a_, b_ in aev)
+    total_ms = multi.max_over_ranks(sum(step_ms), pg, dev)
+    ms = total_ms / args.steps
+    nkd = float(N) * K * d
+    dp = 64 if d <= 64 else 128
+    kpad = (ke + 127) // 128 * 128
+    tensor_flops = 3 * 2.0 * N * kpad * dp
+    peaks = measured_peaks()
+    peak = peaks["bf16_tflops"] if peaks else 1900.0
+    achieved = tensor_flops / (a_ms / 1e3) / 1e12
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+
+        # about 1.2e10 FP64 distance terms: N_s x (ell x rounds) x d
+        n_s = int(min(N, max(4 * K, 1.2e10 / (ell * R * d))))
+        xs = x[:n_s].cpu().numpy()
+        t0 = time.perf_counter()
+        o = oracle.kmeans_par(xs, K, ell, R, seed, sid, cand_cap=min(n_s, cap))
+        dt = time.perf_counter() - t0
+        cores, model = cpu_info()
+        cpu = {"value": n_s * K * d / dt, "unit": "N*K*d/s", "cores": 1, "kind": "oracle",
+               "sample": f"k-means|| on the first {n_s} of {N} points (same K, ell, rounds), "
+                         f"{len(o['cand'])} candidates, serial FP64",
+               "seconds": dt, "host_cores": cores, "cpu": model}
+    if rank == 0:
+        launches = 7 + 8 * R  # prepare, c_0, phi; 8 per round; weights, transpose, recluster, out
+        print(json.dumps({
+            "metric": "k-means|| initialisation N*K*d/s (oversampling + weighted recluster)",
+            "value": nkd * world * args.steps / (total_ms / 1e3), "unit": "N*K*d/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "N": N, "d": d, "K": K, "ell": ell,
+                       "rounds": R, "candidates": n_cand, "status": int(r["status"]),
+                       "parallelism": f"replicas{world}",
+                       "l2": "flushed between steps (512 MiB write)",
+                       "phi_after_rounds": float(r["phi"].item()),
+                       "assign_ms_at_ell": a_ms},
+            "clocks": clocks, "e2e": None, "gpu_launches": launches * args.steps,
+            "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak,
+                         "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                         "kernel": "lloyd_assign_kernel",
+                         "launch": f"kpp_lloyd_assign, N={N}, K={ke} candidates",
+                         "tensor_flops_per_launch": tensor_flops,
+                         "peak_source": "measured bf16 (burst)" if peaks else "fallback"},
+            "cpu_baseline": cpu,
+        }), flush=True)
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -579,6 +700,9 @@ def main():
         return
     if args.workload.startswith(LLOYD_PREFIX):
         run_lloyd(args, rank, world, dev, pg, barrier)
+        return
+    if args.workload.startswith(KMPAR_PREFIX):
+        run_kmpar(args, rank, world, dev, pg, barrier)
         return
     wl = datagen.WORKLOADS[args.workload]
     if args.n_points or args.k_seeds:
