@@ -2,7 +2,7 @@
 // Bahmani et al., which the paper's introduction cites beside k-means++.
 //
 //   * c_0 is the first k-means++ seed; D^2 is the FP32 difference-form
-//     distance to it (the seeding pass's arithmetic), phi its FP64 sum.
+//     distance to it (the seeding pass's arithmetic), phi its sum.
 //   * Each round draws one Bernoulli per point, u_{r,i} < ell D^2_i / phi in
 //     FP64, and appends the chosen points in increasing index (per-CTA
 //     counts, one scan, an ordered compaction).  The points' nearest new
@@ -15,12 +15,14 @@
 //     an equal distance with an earlier position), so the weights are one
 //     histogram at the end.
 //   * The weighted k-means++ recluster over the candidates is sequential in
-//     K and small (a few thousand candidates): one CTA of 1024 threads, each
-//     owning a contiguous run of candidates, FP32 distances, FP64 values
-//     w_c D^2_c, a block scan for the inverse CDF.
+//     K and small (a few thousand candidates): one thread-block cluster of up
+//     to 16 CTAs, each holding a slice of the candidates in shared memory,
+//     FP32 distances, values w_c D^2_c as FP32 two-sum pairs, a cluster-wide
+//     prefix through distributed shared memory for the inverse CDF.
 //
-// Per-CTA sums are FP64 over a fixed partition of the points and combined in
-// CTA order, so a run is deterministic.
+// Per-CTA sums are FP32 two-sum pairs over a fixed partition of the points,
+// combined in CTA order, so a run is deterministic; FP64 appears only in the
+// Bernoulli test near its boundary and in the draw decisions near a tie.
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
@@ -421,8 +423,10 @@ __global__ void kmpar_weights_out_kernel(const unsigned long long *w, int64_t n,
 //      crossing it takes its last candidate with a positive value, and if no
 //      CTA's prefix exceeds t the last CTA with a positive total does the
 //      same (the clamp of the inverse CDF);
-//   4. after a second cluster barrier every CTA reads the pick from that
-//      CTA's shared memory and loads the new centre.
+//   4. that CTA writes the new centre's coordinates into every CTA's shared
+//      memory, and a second cluster barrier completes the step.
+// The draws are computed 32 at a time, one per lane of warp 0, ahead of the
+// steps that use them.
 // T = 0 at a draw (fewer than K candidates carry weight) is a degenerate
 // stop: the remaining indices are -1.
 // ---------------------------------------------------------------------------
@@ -478,7 +482,7 @@ __global__ void __launch_bounds__(kRecThreads, 1) kmpar_recluster_kernel(RecArgs
     __shared__ Thresh s_th;
     __shared__ int s_des, s_clamp;
     __shared__ unsigned long long s_pick;
-    __shared__ long long s_last, s_res;
+    __shared__ long long s_last;
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5, nw = blockDim.x >> 5;
     const int64_t lo = (int64_t)rank * a.slice;
     const int64_t hi = lo + a.slice < a.nc ? lo + a.slice : a.nc;
@@ -495,7 +499,12 @@ __global__ void __launch_bounds__(kRecThreads, 1) kmpar_recluster_kernel(RecArgs
             for (int64_t c = lo + t; c < hi; c += blockDim.x)
                 s_x[(int64_t)j * a.slice + (c - lo)] = a.cT[(int64_t)j * a.ldc + c];
     __syncthreads();
+    double udraw = 0.0; // warp 0: lane l holds the draw of step 32 q + l
     for (int m = 0; m < a.K; ++m) {
+        if (warp == 0 && (m & 31) == 0)
+            udraw = m + lane < a.K
+                        ? philox_uniform_ctr(a.seed, a.stream, (uint64_t)(m + lane), 0, 1, 0)
+                        : 0.0;
         // 1. this thread's run
         Pair seg{};
         long long last = -1;
@@ -556,7 +565,7 @@ __global__ void __launch_bounds__(kRecThreads, 1) kmpar_recluster_kernel(RecArgs
             Pair tex;
             const Pair ti = warp_pair_scan(tv, tex);
             const Pair T = shfl_pair(ti, 31);
-            Thresh th = thresh_for_u(philox_uniform_ctr(a.seed, a.stream, (uint64_t)m, 0, 1, 0));
+            Thresh th = thresh_for_u(__shfl_sync(0xffffffffu, udraw, m & 31));
             thresh_set_total(th, T);
             const unsigned cm = __ballot_sync(0xffffffffu, lane < C && th.gt(ti));
             const unsigned pm = __ballot_sync(0xffffffffu, lane < C && tv.hi > 0.f);
@@ -602,19 +611,18 @@ __global__ void __launch_bounds__(kRecThreads, 1) kmpar_recluster_kernel(RecArgs
             if (last >= 0)
                 atomicMax(&s_last, last);
             __syncthreads();
+            // 4. it writes the new centre into every CTA's shared memory
+            const long long pick = s_pick != ~0ull ? (long long)s_pick : s_last;
+            for (int j = t; j < a.d; j += blockDim.x) {
+                const float v = a.staged ? s_x[(int64_t)j * a.slice + (pick - lo)]
+                                         : a.cbuf[pick * a.d + j];
+                for (int r = 0; r < C; ++r)
+                    *cl.map_shared_rank(&cen[j], (unsigned)r) = v;
+            }
             if (t == 0)
-                s_res = s_pick != ~0ull ? (long long)s_pick : s_last;
-        }
-        cl.sync(); // the pick is published
-        // 4. every CTA takes the new centre
-        if (t < a.d) {
-            const long long pick = *cl.map_shared_rank(&s_res, (unsigned)des);
-            for (int j = t; j < a.d; j += blockDim.x)
-                cen[j] = a.cbuf[pick * a.d + j];
-            if (t == 0 && rank == 0)
                 a.idx_out[m] = a.cand[pick];
         }
-        __syncthreads();
+        cl.sync(); // the new centre is in place everywhere
     }
     cl.sync(); // no CTA leaves while another may still read its shared memory
 }
