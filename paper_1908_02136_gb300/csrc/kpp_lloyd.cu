@@ -336,6 +336,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                         tmem_ld32_async(base + h * 32, r[0]);
                         tmem_ld32_async(base + h * 32 + 32, r[1]);
                         tmem_ld_wait();
+                        tmem_regs_ready(r[0]);
+                        tmem_regs_ready(r[1]);
 #pragma unroll
                         for (int c = 0; c < 2; ++c) {
 #pragma unroll

@@ -159,6 +159,15 @@ __device__ __forceinline__ void tmem_ld_wait()
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// Keeps the compiler from moving uses of `r` above the preceding
+// tcgen05.wait::ld (the wait names no registers, so nothing else orders them).
+__device__ __forceinline__ void tmem_regs_ready(uint32_t (&r)[32])
+{
+#pragma unroll
+    for (int i = 0; i < 32; ++i)
+        asm volatile("" : "+r"(r[i]));
+}
+
 // 32 consecutive 32-bit columns of this thread's TMEM lane (the warp reads
 // its 32-lane quarter).
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32])
