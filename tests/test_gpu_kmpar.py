@@ -194,3 +194,51 @@ def test_deterministic():
     b = _run(x, 16, 4, 5, 32.0)
     for k in ("cand", "weights", "idx", "labels", "d2", "phi"):
         assert np.array_equal(a[k], b[k]), k
+
+
+@pytest.mark.slow
+def test_full_size_workload_sampled():
+    """10^7 x 64, K = 1024, ell = 2K, 5 rounds (the k-means|| bench workload):
+    the last round replayed exactly, D^2 of sampled rows against the FP64
+    nearest candidate, weights, and the recluster replayed on the
+    candidates' rows."""
+    wl = datagen.WORKLOADS["gmm-N1e7-d64-K1024"]
+    N, d, K = wl.N, wl.d, wl.K
+    ell, seed, stream = 2.0 * K, wl.draw_seed, 0
+    x = datagen.workload_points(wl, DEV)
+    r4 = kpp.kmeans_par(x, K, seed, stream, ell=ell, rounds=4)
+    r5 = kpp.kmeans_par(x, K, seed, stream, ell=ell, rounds=5)
+    torch.cuda.synchronize()
+    assert r5["status"] == kpp.OK
+    c4, c5 = r4["cand"].cpu().numpy(), r5["cand"].cpu().numpy()
+    assert c5[0] == min(int(oracle.uniform(seed, stream, 0) * N), N - 1)
+    assert np.array_equal(c5[:c4.size], c4) and len(np.unique(c5)) == c5.size
+    # the fifth round's Bernoulli decisions, replayed on the fourth's D^2 and phi
+    flags, _, _ = oracle.kmpar_select(r4["d2"].cpu().numpy().astype(np.float64),
+                                      float(r4["phi"].cpu()[0]), ell, seed, stream, 4)
+    assert np.array_equal(c5[c4.size:], np.flatnonzero(flags))
+    # weights: a histogram of the nearest candidates; every candidate holds itself
+    w = r5["weights"].cpu().numpy()
+    lab = r5["labels"].cpu().numpy()
+    assert w.sum() == N and np.all(w >= 1)
+    assert np.array_equal(lab[c5], np.arange(c5.size))
+    # sampled D^2 against the FP64 nearest candidate
+    rows = np.sort(np.random.default_rng(3).choice(N, 2000, replace=False))
+    X = x[torch.as_tensor(rows, device=DEV)].cpu().numpy().astype(np.float64)
+    C = x[r5["cand"]].cpu().numpy().astype(np.float64)
+    arg, best = _nearest(X, C)
+    d2 = r5["d2"].cpu().numpy()[rows].astype(np.float64)
+    held = ((X - C[lab[rows]]) ** 2).sum(1)
+    nz = held > 0  # a sampled row may be a candidate itself
+    assert np.all(d2[~nz] == 0)
+    assert np.max(np.abs(d2[nz] - held[nz]) / held[nz]) <= 1e-5
+    bound = 2.0 ** -12 * np.linalg.norm(X, axis=1) * np.linalg.norm(C, axis=1).max()
+    assert np.all(held - best <= bound)
+    assert np.mean(lab[rows] != arg) <= 0.05
+    # the recluster, replayed on the candidates' own rows
+    idx = r5["idx"].cpu().numpy()
+    pos_of = {int(c): i for i, c in enumerate(c5)}
+    pos = np.array([pos_of[int(i)] for i in idx])
+    _, own, st = oracle.weighted_seed(C.astype(np.float32), np.arange(c5.size), w, K, seed,
+                                      stream, forced=pos)
+    assert st == 0 and np.sum(own != pos) <= 1
