@@ -403,30 +403,28 @@ __global__ void kmpar_weights_out_kernel(const unsigned long long *w, int64_t n,
 
 // ---------------------------------------------------------------------------
 // Step 4: weighted k-means++ over the nc candidates, on one thread-block
-// cluster (up to 16 CTAs, one per SM, so the per-step L2 reads of the
-// candidates' coordinates spread over that many SMs).  CTA r owns the
-// contiguous slice [r S, r S + S) of the candidate list, thread t of it the
-// contiguous run [t R, t R + R) of the slice; D^2 and the weights of the
-// slice stay in shared memory, the coordinates are read feature-major (cT,
-// coalesced across a warp).  Per centre m:
+// cluster (up to 16 CTAs, one per SM, so the per-step work spreads over that
+// many SMs).  CTA r owns the contiguous slice [r S, r S + S) of the
+// candidate list, thread t of it the contiguous run [t R, t R + R) of the
+// slice; coordinates (feature-major), D^2 and the weights of the slice stay
+// in shared memory.  Per centre m:
 //   1. every thread updates D^2 of its run to the last centre (FP32
 //      difference form, features in order), forms v = w D^2 as an FP32
 //      two-sum pair (w split into two floats, products with their exact
-//      FMA error terms) and sums its run in order;
-//   2. a CTA scan gives the slice total, which every CTA reads from every
-//      other CTA's shared memory after a cluster barrier; all CTAs prefix
-//      the totals in rank order the same way, so they agree on T, on the
-//      threshold t = v_m T and on the CTA whose prefix first exceeds t;
-//   3. that CTA walks its runs from its exclusive prefix and takes the first
-//      candidate whose running prefix exceeds t (decided in FP32 pairs, or
-//      exactly in FP64 when within 2^-40 t of it); if rounding leaves no
-//      crossing it takes its last candidate with a positive value, and if no
-//      CTA's prefix exceeds t the last CTA with a positive total does the
-//      same (the clamp of the inverse CDF);
-//   4. that CTA writes the new centre's coordinates into every CTA's shared
-//      memory, and a second cluster barrier completes the step.
-// The draws are computed 32 at a time, one per lane of warp 0, ahead of the
-// steps that use them.
+//      FMA error terms), sums its run in order and publishes the sum; each
+//      warp publishes its total;
+//   2. after a cluster barrier, warp 0 of every CTA reads all warp totals of
+//      all CTAs from distributed shared memory and sums them in the same
+//      order, so every CTA agrees on T, on the threshold t = v_m T and on the
+//      CTA whose prefix first exceeds t;
+//   3. warp 0 of that CTA narrows the crossing to a warp, a thread and an
+//      element of its run (decisions in FP32 pairs, exactly in FP64 when
+//      within 2^-40 t; at any level where rounding leaves no crossing, the
+//      last element with a positive value -- the clamp of the inverse CDF)
+//      and writes the new centre's coordinates into every CTA's shared
+//      memory; a second cluster barrier completes the step.
+// Only the two cluster barriers synchronise a step.  The draws are computed
+// 32 at a time, one per lane of warp 0, ahead of the steps that use them.
 // T = 0 at a draw (fewer than K candidates carry weight) is a degenerate
 // stop: the remaining indices are -1.
 // ---------------------------------------------------------------------------
@@ -464,6 +462,29 @@ __device__ __forceinline__ Pair weighted(float whi, float wlo, float r)
     return v;
 }
 
+// Over n <= 32 lanes holding values v (lanes at or past n hold zero): the
+// first lane whose running prefix base + v_0 + .. + v_l exceeds the threshold
+// (-1 if none), the last lane with a positive value (-1 if none), and the
+// prefix before the lane taken (the first, else the last).  Every lane
+// returns the same.
+__device__ __forceinline__ void lane_cross(const Pair &v, const Pair &base, const Thresh &th,
+                                           int &first, int &last, Pair &before)
+{
+    Pair ex;
+    const Pair inc = warp_pair_scan(v, ex);
+    Pair P = base;
+    P.add(inc);
+    const bool pos = v.hi > 0.f;
+    const unsigned cm = __ballot_sync(0xffffffffu, pos && th.gt(P));
+    const unsigned pm = __ballot_sync(0xffffffffu, pos);
+    first = cm ? __ffs(cm) - 1 : -1;
+    last = pm ? 31 - __clz(pm) : -1;
+    const int sel = first >= 0 ? first : (last >= 0 ? last : 0);
+    Pair B = base;
+    B.add(ex);
+    before = shfl_pair(B, sel);
+}
+
 __global__ void __launch_bounds__(kRecThreads, 1) kmpar_recluster_kernel(RecArgs a)
 {
     namespace cg = cooperative_groups;
@@ -476,13 +497,9 @@ __global__ void __launch_bounds__(kRecThreads, 1) kmpar_recluster_kernel(RecArgs
     float *s_rd2 = rsm, *s_whi = rsm + a.slice, *s_wlo = rsm + 2 * a.slice;
     float *s_x = rsm + 3 * a.slice;
     __shared__ float cen[kMaxD];
-    __shared__ Pair s_wx[kRecThreads / 32]; // warp totals, then their exclusive prefix
-    __shared__ Pair s_cta;                  // this CTA's total (read by the cluster)
-    __shared__ Pair s_E;                    // prefix before this CTA
-    __shared__ Thresh s_th;
-    __shared__ int s_des, s_clamp;
-    __shared__ unsigned long long s_pick;
-    __shared__ long long s_last;
+    __shared__ Pair s_seg[kRecThreads];     // each thread's run sum
+    __shared__ Pair s_wt[kRecThreads / 32]; // each warp's total
+    __shared__ int s_stop;
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5, nw = blockDim.x >> 5;
     const int64_t lo = (int64_t)rank * a.slice;
     const int64_t hi = lo + a.slice < a.nc ? lo + a.slice : a.nc;
@@ -498,6 +515,8 @@ __global__ void __launch_bounds__(kRecThreads, 1) kmpar_recluster_kernel(RecArgs
         for (int j = 0; j < a.d; ++j)
             for (int64_t c = lo + t; c < hi; c += blockDim.x)
                 s_x[(int64_t)j * a.slice + (c - lo)] = a.cT[(int64_t)j * a.ldc + c];
+    if (t == 0)
+        s_stop = 0;
     __syncthreads();
     double udraw = 0.0; // warp 0: lane l holds the draw of step 32 q + l
     for (int m = 0; m < a.K; ++m) {
@@ -505,9 +524,8 @@ __global__ void __launch_bounds__(kRecThreads, 1) kmpar_recluster_kernel(RecArgs
             udraw = m + lane < a.K
                         ? philox_uniform_ctr(a.seed, a.stream, (uint64_t)(m + lane), 0, 1, 0)
                         : 0.0;
-        // 1. this thread's run
+        // 1. this thread's run: D^2 to the last centre, values, their sum
         Pair seg{};
-        long long last = -1;
         for (int64_t c = r0; c < r1; ++c) {
             const int li = (int)(c - lo);
             Pair v;
@@ -537,92 +555,90 @@ __global__ void __launch_bounds__(kRecThreads, 1) kmpar_recluster_kernel(RecArgs
                 v = weighted(s_whi[li], s_wlo[li], r);
             }
             seg.add(v);
-            if (v.hi > 0.f)
-                last = c;
         }
-        // 2. CTA scan, then the cluster's totals
-        Pair ex;
-        const Pair inc = warp_pair_scan(seg, ex);
-        if (lane == 31)
-            s_wx[warp] = inc;
-        __syncthreads();
+        s_seg[t] = seg;
+        const Pair wtot = warp_pair_sum(seg);
+        if (lane == 0)
+            s_wt[warp] = wtot;
+        cl.sync(); // every thread's and warp's sum is published
         if (warp == 0) {
-            const Pair wv = lane < nw ? s_wx[lane] : Pair{};
-            Pair wex;
-            const Pair wi = warp_pair_scan(wv, wex);
-            if (lane < nw)
-                s_wx[lane] = wex;
-            if (lane == 31)
-                s_cta = wi;
-            if (lane == 0) {
-                s_pick = ~0ull;
-                s_last = -1;
+            // 2. the CTA totals in rank order, from every CTA's warp totals
+            Pair ct{};
+            if (lane < C) {
+                const Pair *rw = cl.map_shared_rank(s_wt, (unsigned)lane);
+#pragma unroll 4
+                for (int w = 0; w < nw; ++w)
+                    ct.add(rw[w]);
             }
-        }
-        cl.sync(); // every CTA's total is published
-        if (warp == 0) {
-            const Pair tv = lane < C ? *cl.map_shared_rank(&s_cta, (unsigned)lane) : Pair{};
-            Pair tex;
-            const Pair ti = warp_pair_scan(tv, tex);
-            const Pair T = shfl_pair(ti, 31);
+            Pair cex;
+            const Pair cinc = warp_pair_scan(ct, cex);
+            const Pair T = shfl_pair(cinc, 31);
             Thresh th = thresh_for_u(__shfl_sync(0xffffffffu, udraw, m & 31));
             thresh_set_total(th, T);
-            const unsigned cm = __ballot_sync(0xffffffffu, lane < C && th.gt(ti));
-            const unsigned pm = __ballot_sync(0xffffffffu, lane < C && tv.hi > 0.f);
-            if (lane == rank)
-                s_E = tex;
-            if (lane == 0) {
-                s_th = th;
-                s_des = cm ? __ffs(cm) - 1 : (pm ? 31 - __clz(pm) : -1);
-                s_clamp = cm ? 0 : 1;
-            }
-        }
-        __syncthreads();
-        const Thresh th = s_th;
-        const int des = s_des;
-        if (!(th.T.hi > 0.f) || des < 0) {
-            // degenerate stop
-            if (rank == 0) {
-                if (t == 0)
-                    atomicCAS(&a.ctl->status, KPP_OK, KPP_ERR_DEGENERATE);
-                for (int k = m + t; k < a.K; k += blockDim.x)
-                    a.idx_out[k] = -1;
-            }
-            cl.sync();
-            return;
-        }
-        // 3. the designated CTA finds the crossing
-        if (rank == des) {
-            if (!s_clamp) {
-                Pair P = s_E;
-                P.add(s_wx[warp]);
-                P.add(ex);
-                for (int64_t c = r0; c < r1; ++c) {
-                    const int li = (int)(c - lo);
-                    const Pair v = m == 0 ? Pair{s_whi[li], s_wlo[li]}
-                                          : weighted(s_whi[li], s_wlo[li], s_rd2[li]);
-                    P.add(v);
-                    if (v.hi > 0.f && th.gt(P)) {
-                        atomicMin(&s_pick, (unsigned long long)c);
-                        break;
+            if (!(T.hi > 0.f)) {
+                // degenerate stop
+                if (rank == 0) {
+                    if (lane == 0)
+                        atomicCAS(&a.ctl->status, KPP_OK, KPP_ERR_DEGENERATE);
+                    for (int k = m + lane; k < a.K; k += 32)
+                        a.idx_out[k] = -1;
+                }
+                if (lane == 0)
+                    s_stop = 1;
+            } else {
+                const unsigned cm = __ballot_sync(0xffffffffu, ct.hi > 0.f && th.gt(cinc));
+                const unsigned pm = __ballot_sync(0xffffffffu, ct.hi > 0.f);
+                const int des = cm ? __ffs(cm) - 1 : 31 - __clz(pm);
+                bool clamp = cm == 0;
+                if (rank == des) {
+                    // 3. narrow the crossing to a warp, a thread, an element
+                    const Pair base = shfl_pair(cex, des);
+                    int f, l;
+                    Pair before;
+                    lane_cross(lane < nw ? s_wt[lane] : Pair{}, base, th, f, l, before);
+                    const int ws = !clamp && f >= 0 ? f : l;
+                    clamp = clamp || f < 0;
+                    lane_cross(s_seg[ws * 32 + lane], before, th, f, l, before);
+                    const int tt = ws * 32 + (!clamp && f >= 0 ? f : l);
+                    clamp = clamp || f < 0;
+                    const int64_t e0 = lo + (int64_t)tt * a.run < hi ? lo + (int64_t)tt * a.run : hi;
+                    const int64_t e1 = e0 + a.run < hi ? e0 + a.run : hi;
+                    long long pick = -1;
+                    if (lane == 0) {
+                        Pair P = before;
+                        long long lastp = -1;
+                        for (int64_t c = e0; c < e1; ++c) {
+                            const int li = (int)(c - lo);
+                            const Pair v = m == 0 ? Pair{s_whi[li], s_wlo[li]}
+                                                  : weighted(s_whi[li], s_wlo[li], s_rd2[li]);
+                            if (!(v.hi > 0.f))
+                                continue;
+                            lastp = c;
+                            P.add(v);
+                            if (!clamp && th.gt(P)) {
+                                pick = c;
+                                break;
+                            }
+                        }
+                        if (pick < 0)
+                            pick = lastp;
                     }
+                    pick = __shfl_sync(0xffffffffu, pick, 0);
+                    // 4. the new centre into every CTA's shared memory
+                    for (int j = lane; j < a.d; j += 32) {
+                        const float v = a.staged ? s_x[(int64_t)j * a.slice + (pick - lo)]
+                                                 : a.cbuf[pick * a.d + j];
+                        for (int r = 0; r < C; ++r)
+                            *cl.map_shared_rank(&cen[j], (unsigned)r) = v;
+                    }
+                    if (lane == 0)
+                        a.idx_out[m] = a.cand[pick];
                 }
             }
-            if (last >= 0)
-                atomicMax(&s_last, last);
-            __syncthreads();
-            // 4. it writes the new centre into every CTA's shared memory
-            const long long pick = s_pick != ~0ull ? (long long)s_pick : s_last;
-            for (int j = t; j < a.d; j += blockDim.x) {
-                const float v = a.staged ? s_x[(int64_t)j * a.slice + (pick - lo)]
-                                         : a.cbuf[pick * a.d + j];
-                for (int r = 0; r < C; ++r)
-                    *cl.map_shared_rank(&cen[j], (unsigned)r) = v;
-            }
-            if (t == 0)
-                a.idx_out[m] = a.cand[pick];
         }
         cl.sync(); // the new centre is in place everywhere
+        if (s_stop)
+            break;
     }
     cl.sync(); // no CTA leaves while another may still read its shared memory
 }
