@@ -39,7 +39,9 @@ constexpr int kGrid = 1024;        // their CTAs; each owns a contiguous range o
 constexpr int kChunk = 4096;       // candidates per tensor-core assignment (its K limit)
 constexpr int kMaxD = 128;
 constexpr int kRecThreads = 1024;  // recluster CTA
-constexpr int kRowsInFlight = 8;   // rows a warp loads before reducing (<= 32)
+// rows a warp loads before reducing, by features per lane (VEC = ceil(d/32)):
+// 16 rows of one or two registers, 8 of four (<= 32: lane q owns row q)
+template <int VEC> __host__ __device__ constexpr int rows_in_flight() { return VEC == 4 ? 8 : 16; }
 constexpr size_t kAlign = 256;
 
 size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
@@ -106,11 +108,12 @@ Layout layout(int64_t N, int32_t d, int64_t cand_cap)
 // lane partials are combined by an xor butterfly, so every lane ends with
 // the same FP32 value.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float lane_sq(const float (&xv)[4], const float *c, int d, int lane)
+template <int VEC>
+__device__ __forceinline__ float lane_sq(const float (&xv)[VEC], const float *c, int d, int lane)
 {
     float s = 0.f;
 #pragma unroll
-    for (int v = 0; v < 4; ++v) {
+    for (int v = 0; v < VEC; ++v) {
         const int j = lane + 32 * v;
         if (j < d) {
             const float t = xv[v] - c[j];
@@ -123,11 +126,12 @@ __device__ __forceinline__ float lane_sq(const float (&xv)[4], const float *c, i
     return s;
 }
 
+template <int VEC>
 __device__ __forceinline__ void load_row(const float *x, int64_t row, int d, int lane, bool ok,
-                                         float (&xv)[4])
+                                         float (&xv)[VEC])
 {
 #pragma unroll
-    for (int v = 0; v < 4; ++v) {
+    for (int v = 0; v < VEC; ++v) {
         const int j = lane + 32 * v;
         xv[v] = (ok && j < d) ? __ldcs(x + row * d + j) : 0.f;
     }
@@ -151,6 +155,7 @@ __device__ __forceinline__ Pair cta_sum_ordered(const Pair &v, Pair *sh)
 // ---------------------------------------------------------------------------
 // Step 1: c_0, D^2 to it, labels 0.
 // ---------------------------------------------------------------------------
+template <int VEC>
 __global__ void __launch_bounds__(kThreads) kmpar_init_kernel(const float *x, int64_t N, int d,
                                                               int64_t range, uint64_t seed,
                                                               uint64_t stream, float *D2,
@@ -173,11 +178,12 @@ __global__ void __launch_bounds__(kThreads) kmpar_init_kernel(const float *x, in
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     const int64_t lo = blockIdx.x * range, hi = lo + range < N ? lo + range : N;
+    constexpr int kRowsInFlight = rows_in_flight<VEC>();
     // a warp takes kRowsInFlight rows at a time; lane q keeps row q's
     // result, so the D^2 and label stores of a batch are one coalesced store
     Pair acc{};
     for (int64_t r0 = lo + (int64_t)warp * kRowsInFlight; r0 < hi; r0 += (int64_t)nw * kRowsInFlight) {
-        float xv[kRowsInFlight][4];
+        float xv[kRowsInFlight][VEC];
 #pragma unroll
         for (int q = 0; q < kRowsInFlight; ++q)
             load_row(x, r0 + q, d, lane, r0 + q < hi, xv[q]);
@@ -340,6 +346,7 @@ __global__ void __launch_bounds__(kThreads)
 // Step 2d: D^2 = min(D^2, exact distance to the candidate the tensor-core
 // assignment picked among cbuf[base .. base + n)); a tie goes to the earlier
 // position.  Writes the CTA's FP64 sum of the resulting D^2.
+template <int VEC>
 __global__ void __launch_bounds__(kThreads)
     kmpar_min_update_kernel(const float *x, int64_t N, int d, int64_t range, const float *cbuf,
                             int64_t base, int32_t n, const int32_t *pick, float *D2, int32_t *lab,
@@ -348,6 +355,7 @@ __global__ void __launch_bounds__(kThreads)
     __shared__ Pair sh[kThreads / 32];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     const int64_t lo = blockIdx.x * range, hi = lo + range < N ? lo + range : N;
+    constexpr int kRowsInFlight = rows_in_flight<VEC>();
     Pair acc{};
     for (int64_t r0 = lo + (int64_t)warp * kRowsInFlight; r0 < hi; r0 += (int64_t)nw * kRowsInFlight) {
         // lane q < kRowsInFlight loads row q's label, D^2 and nearest so far
@@ -359,7 +367,7 @@ __global__ void __launch_bounds__(kThreads)
         pk = (unsigned)pk < (unsigned)n ? pk : 0;
         float cur = own ? D2[row] : 0.f;
         const int32_t l = own ? lab[row] : 0;
-        float xv[kRowsInFlight][4];
+        float xv[kRowsInFlight][VEC];
 #pragma unroll
         for (int q = 0; q < kRowsInFlight; ++q)
             load_row(x, r0 + q, d, lane, r0 + q < hi, xv[q]);
@@ -413,17 +421,18 @@ __global__ void kmpar_weights_out_kernel(const unsigned long long *w, int64_t n,
 //      two-sum pair (w split into two floats, products with their exact
 //      FMA error terms), sums its run in order and publishes the sum; each
 //      warp publishes its total;
-//   2. after a cluster barrier, warp 0 of every CTA reads all warp totals of
-//      all CTAs from distributed shared memory and sums them in the same
-//      order, so every CTA agrees on T, on the threshold t = v_m T and on the
-//      CTA whose prefix first exceeds t;
+//   2. after a cluster barrier, warp c of every CTA sums CTA c's warp totals
+//      read from distributed shared memory, and warp 0 prefixes the CTA
+//      totals in rank order; every CTA does the same arithmetic on the same
+//      values, so all agree on T, on the threshold t = v_m T and on the CTA
+//      whose prefix first exceeds t;
 //   3. warp 0 of that CTA narrows the crossing to a warp, a thread and an
 //      element of its run (decisions in FP32 pairs, exactly in FP64 when
 //      within 2^-40 t; at any level where rounding leaves no crossing, the
 //      last element with a positive value -- the clamp of the inverse CDF)
 //      and writes the new centre's coordinates into every CTA's shared
 //      memory; a second cluster barrier completes the step.
-// Only the two cluster barriers synchronise a step.  The draws are computed
+// A step synchronises at two cluster barriers and one CTA barrier.  The draws are computed
 // 32 at a time, one per lane of warp 0, ahead of the steps that use them.
 // T = 0 at a draw (fewer than K candidates carry weight) is a degenerate
 // stop: the remaining indices are -1.
@@ -499,6 +508,7 @@ __global__ void __launch_bounds__(kRecThreads, 1) kmpar_recluster_kernel(RecArgs
     __shared__ float cen[kMaxD];
     __shared__ Pair s_seg[kRecThreads];     // each thread's run sum
     __shared__ Pair s_wt[kRecThreads / 32]; // each warp's total
+    __shared__ Pair s_ct[kRecMaxCluster];   // each CTA's total
     __shared__ int s_stop;
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5, nw = blockDim.x >> 5;
     const int64_t lo = (int64_t)rank * a.slice;
@@ -561,15 +571,17 @@ __global__ void __launch_bounds__(kRecThreads, 1) kmpar_recluster_kernel(RecArgs
         if (lane == 0)
             s_wt[warp] = wtot;
         cl.sync(); // every thread's and warp's sum is published
+        // 2. warp c sums CTA c's warp totals (one remote load per lane); warp
+        // 0 then prefixes the CTA totals in rank order
+        for (int c = warp; c < C; c += nw) {
+            const Pair *rw = cl.map_shared_rank(s_wt, (unsigned)c);
+            const Pair v = warp_pair_sum(lane < nw ? rw[lane] : Pair{});
+            if (lane == 0)
+                s_ct[c] = v;
+        }
+        __syncthreads();
         if (warp == 0) {
-            // 2. the CTA totals in rank order, from every CTA's warp totals
-            Pair ct{};
-            if (lane < C) {
-                const Pair *rw = cl.map_shared_rank(s_wt, (unsigned)lane);
-#pragma unroll 4
-                for (int w = 0; w < nw; ++w)
-                    ct.add(rw[w]);
-            }
+            const Pair ct = lane < C ? s_ct[lane] : Pair{};
             Pair cex;
             const Pair cinc = warp_pair_scan(ct, cex);
             const Pair T = shfl_pair(cinc, 31);
@@ -802,8 +814,12 @@ kpp_status kpp_kmeans_par(const float *points, int64_t N, int32_t d, int32_t K, 
     kpp_status st = kpp_lloyd_prepare(points, N, d, kl, lws, L.lloyd_bytes, stream);
     if (st != KPP_OK)
         return st;
-    kmpar_init_kernel<<<kGrid, kThreads, 0, s>>>(points, N, d, L.range, seed, stream_id, D2, lab,
-                                                 cand_out, cbuf, part);
+    auto init_fn = d <= 32 ? &kmpar_init_kernel<1> : d <= 64 ? &kmpar_init_kernel<2>
+                                                             : &kmpar_init_kernel<4>;
+    auto update_fn = d <= 32 ? &kmpar_min_update_kernel<1>
+                             : d <= 64 ? &kmpar_min_update_kernel<2> : &kmpar_min_update_kernel<4>;
+    init_fn<<<kGrid, kThreads, 0, s>>>(points, N, d, L.range, seed, stream_id, D2, lab, cand_out,
+                                       cbuf, part);
     kmpar_phi_kernel<<<1, 32, 0, s>>>(part, kGrid, sc);
     if (!launched())
         return KPP_ERR_LAUNCH;
@@ -834,9 +850,8 @@ kpp_status kpp_kmeans_par(const float *points, int64_t N, int32_t d, int32_t K, 
             st = kpp_lloyd_assign(cbuf + (nc + c0) * d, N, d, kc, pick, lws, L.lloyd_bytes, stream);
             if (st != KPP_OK)
                 return st;
-            kmpar_min_update_kernel<<<kGrid, kThreads, 0, s>>>(points, N, d, L.range, cbuf,
-                                                               nc + c0, kc, pick, D2, lab,
-                                                               part);
+            update_fn<<<kGrid, kThreads, 0, s>>>(points, N, d, L.range, cbuf, nc + c0, kc, pick,
+                                                 D2, lab, part);
         }
         kmpar_phi_kernel<<<1, 32, 0, s>>>(part, kGrid, sc);
         if (!launched())
