@@ -133,6 +133,7 @@ struct AssignArgs {
     int32_t K;
     int32_t nk;     // feature chunks (dp / 64)
     int32_t stages; // centre-tile stages in shared memory
+    int32_t abufs;  // point-tile buffers (2: the next group's load overlaps this one)
     const float *cn;
     int32_t *labels;
     Control *ctl;
@@ -166,19 +167,24 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                                 ~uintptr_t(1023));
     const int NS = a.stages;
-    uint8_t *sA = smem;                              // [tile][plane][chunk] 16 KB each
-    uint8_t *sB = smem + kMT * 2 * a.nk * kABytes;   // [stage][plane] 16 KB each
+    const uint32_t abytes = kMT * 2 * a.nk * kABytes; // one group's point tiles
+    uint8_t *sA = smem;                              // [buffer][tile][plane][chunk] 16 KB each
+    uint8_t *sB = smem + a.abufs * abytes;           // [stage][plane] 16 KB each
     float *s_cn = reinterpret_cast<float *>(sB + NS * 2 * kBBytes);
-    __shared__ uint64_t a_full, a_empty, b_full[kMaxStages], b_empty[kMaxStages], acc_full[2],
+    __shared__ uint64_t a_full[2], a_empty[2], b_full[kMaxStages], b_empty[kMaxStages], acc_full[2],
         acc_empty[2], done;
     __shared__ uint32_t tmem_base;
     __shared__ volatile int abort_flag;
-    auto a_tile = [&](int t, int plane, int k) { return sA + ((t * 2 + plane) * a.nk + k) * kABytes; };
+    auto a_tile = [&](uint32_t b, int t, int plane, int k) {
+        return sA + b * abytes + ((t * 2 + plane) * a.nk + k) * kABytes;
+    };
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
-        mbar_init(&a_full, 1);
-        mbar_init(&a_empty, 1);
+        for (int s = 0; s < 2; ++s) {
+            mbar_init(&a_full[s], 1);
+            mbar_init(&a_empty[s], 1);
+        }
         for (int s = 0; s < NS; ++s) {
             mbar_init(&b_full[s], 1);
             mbar_init(&b_empty[s], 1);
@@ -209,22 +215,23 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (warp == 0 && lane == 0) {
         // ---- producer ----
         uint32_t it = 0, g = 0;
-        uint32_t a_pending = 0; // 1 + iteration of the last point load issued
+        uint32_t a_pending[2] = {}; // 1 + use of the last point load per buffer
         uint32_t b_pending[kMaxStages] = {}; // 1 + use of the last centre load per stage
         for (int64_t gp = blockIdx.x; gp < n_grp && !abort_flag; gp += gridDim.x, ++it) {
-            if (it > 0 && !mbar_wait(&a_empty, (it - 1) & 1, a.timeout_ns)) {
+            const uint32_t ab = it % a.abufs, ause = it / a.abufs;
+            if (ause > 0 && !mbar_wait(&a_empty[ab], (ause - 1) & 1, a.timeout_ns)) {
                 fail(a.ctl, &abort_flag);
                 break;
             }
-            mbar_expect_tx(&a_full, kMT * 2 * a.nk * kABytes);
+            mbar_expect_tx(&a_full[ab], abytes);
             for (int t = 0; t < kMT; ++t) {
                 const int y = (int)((gp * kMT + t) * kBM);
                 for (int k = 0; k < a.nk; ++k) {
-                    tma_load_2d(a_tile(t, 0, k), &map_phi, &a_full, k * kBK, y);
-                    tma_load_2d(a_tile(t, 1, k), &map_plo, &a_full, k * kBK, y);
+                    tma_load_2d(a_tile(ab, t, 0, k), &map_phi, &a_full[ab], k * kBK, y);
+                    tma_load_2d(a_tile(ab, t, 1, k), &map_plo, &a_full[ab], k * kBK, y);
                 }
             }
-            a_pending = it + 1;
+            a_pending[ab] = ause + 1;
             for (int ct = 0; ct < n_ct && !abort_flag; ++ct) {
                 for (int k = 0; k < a.nk; ++k, ++g) {
                     const uint32_t s = g % NS, use = g / NS;
@@ -241,8 +248,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         if (abort_flag) {
             // let the copies already issued land before the CTA exits
-            if (a_pending)
-                mbar_wait(&a_full, (a_pending - 1) & 1, a.timeout_ns);
+            for (int b = 0; b < 2; ++b)
+                if (a_pending[b])
+                    mbar_wait(&a_full[b], (a_pending[b] - 1) & 1, a.timeout_ns);
             for (int s = 0; s < NS; ++s)
                 if (b_pending[s])
                     mbar_wait(&b_full[s], (b_pending[s] - 1) & 1, a.timeout_ns);
@@ -253,7 +261,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         uint32_t it = 0, g = 0, t = 0;
         bool issued = false;
         for (int64_t gp = blockIdx.x; gp < n_grp && !abort_flag; gp += gridDim.x, ++it) {
-            if (!mbar_wait(&a_full, it & 1, a.timeout_ns)) {
+            const uint32_t ab = it % a.abufs, ause = it / a.abufs;
+            if (!mbar_wait(&a_full[ab], ause & 1, a.timeout_ns)) {
                 fail(a.ctl, &abort_flag);
                 break;
             }
@@ -277,8 +286,8 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
                     for (int mt = 0; mt < kMT; ++mt) {
                         const uint32_t d_tmem = tmem + (buf * kMT + mt) * kBN;
-                        const uint32_t ah = smem_u32(a_tile(mt, 0, k));
-                        const uint32_t al = smem_u32(a_tile(mt, 1, k));
+                        const uint32_t ah = smem_u32(a_tile(ab, mt, 0, k));
+                        const uint32_t al = smem_u32(a_tile(ab, mt, 1, k));
 #pragma unroll
                         for (int kk = 0; kk < kBK / 16; ++kk) {
                             // one MMA covers 16 features = 32 bytes of the swizzled row
@@ -298,7 +307,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             if (abort_flag)
                 break;
-            mma_commit(&a_empty);
+            mma_commit(&a_empty[ab]);
         }
         // every MMA issued has completed before the tensor memory is freed
         if (issued) {
@@ -597,17 +606,22 @@ bool make_map(CUtensorMap *m, const void *base, int64_t rows, int dp, int box_ro
 // centre-tile stages that fit beside the point tiles and the centre norms
 int padded_k(int K) { return (K + kBN - 1) / kBN * kBN; }
 
-int assign_stages(int nk, int K)
+int assign_stages(int nk, int K, int abufs)
 {
-    const size_t budget =
-        227 * 1024 - 1024 - 256 - (size_t)kMT * 2 * nk * kABytes - (size_t)padded_k(K) * 4;
-    const int s = (int)(budget / (2 * kBBytes));
+    const long long budget = 227LL * 1024 - 1024 - 8 * 1024 -
+                             (long long)abufs * kMT * 2 * nk * kABytes - (long long)padded_k(K) * 4;
+    const int s = budget > 0 ? (int)(budget / (2 * kBBytes)) : 0;
     return s < kMaxStages ? s : kMaxStages;
 }
 
+// Two point-tile buffers when that still leaves kMinStagesTwoA centre stages.
+constexpr int kMinStagesTwoA = 2;
+int assign_abufs(int nk, int K) { return assign_stages(nk, K, 2) >= kMinStagesTwoA ? 2 : 1; }
+
 size_t assign_smem(int nk, int K)
 {
-    return 1024 + (size_t)kMT * 2 * nk * kABytes + (size_t)assign_stages(nk, K) * 2 * kBBytes +
+    const int ab = assign_abufs(nk, K);
+    return 1024 + (size_t)ab * kMT * 2 * nk * kABytes + (size_t)assign_stages(nk, K, ab) * 2 * kBBytes +
            (size_t)padded_k(K) * 4;
 }
 
@@ -687,7 +701,8 @@ kpp_status kpp_lloyd_assign(const float *centres, int64_t N, int32_t d, int32_t 
     a.N = N;
     a.K = K;
     a.nk = nk;
-    a.stages = assign_stages(nk, K);
+    a.abufs = assign_abufs(nk, K);
+    a.stages = assign_stages(nk, K, a.abufs);
     a.cn = cn;
     a.labels = labels_out;
     a.ctl = reinterpret_cast<Control *>(ws);
