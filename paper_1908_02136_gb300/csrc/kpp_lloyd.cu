@@ -401,24 +401,25 @@ __host__ __device__ inline int update_tile(int K, int d)
 }
 
 // Every CTA owns a contiguous range of points and walks it once per tile of
-// TK centres.  A warp takes kUpdRows points at a time: their labels in one
-// load, then all their features (lane j holds features j, j+32, ...), so the
-// loads of a batch are in flight together; each point's features are added
-// into the CTA's FP32 sums of its centre in shared memory.  The tile's sums
-// then go to the FP64 totals in global memory with one atomic per (centre,
-// feature).  The first walk also takes the FP32 difference-form D^2 to the
-// assigned centre and the CTA's cost: per lane the squares of its features
-// (even features in one accumulator, odd in another), then the batch's 8
-// per-lane partials are reduce-scattered across the warp (9 shuffles for 8
-// points) and lane 4r holds the D^2 of point r; costs are FP32 two-sum pairs.
-constexpr int kUpdRows = 8;
-
-template <int VEC> // features per lane and point: ceil(d / 32)
+// TK centres.  A warp takes ROWS points at a time (16 for d <= 64, 8 above):
+// their labels in one load, then all their features (lane j holds features
+// j, j+32, ...), so the loads of a batch are in flight together; each point's
+// features are added into the CTA's FP32 sums of its centre in shared memory.
+// Walks after the first load only the points whose centre is in the tile.
+// The tile's sums then go to the FP64 totals in global memory with one atomic
+// per (centre, feature).  The first walk also takes the FP32 difference-form
+// D^2 to the assigned centre and the CTA's cost: per lane the squares of its
+// features (even features in one accumulator, odd in another), then the
+// batch's per-lane partials are reduce-scattered across the warp (point r
+// ends in lane r * 32 / ROWS); costs are FP32 two-sum pairs.
+template <int VEC, int ROWS> // features per lane and point: ceil(d / 32); points per batch
 __global__ void __launch_bounds__(kUpdThreads, 1)
     lloyd_update_kernel(const float *x, int64_t N, int d, int K, const float *c,
                         const int32_t *labels, float *d2_out, double *sums,
                         unsigned long long *counts, double *partial)
 {
+    static_assert(ROWS == 8 || ROWS == 16, "8 or 16 points per batch");
+    constexpr int kStages = ROWS == 16 ? 4 : 3; // reduce-scatter halvings
     extern __shared__ float u_smem[];
     __shared__ float2 wsum[kUpdThreads / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -429,7 +430,7 @@ __global__ void __launch_bounds__(kUpdThreads, 1)
     const int64_t per = (N + gridDim.x - 1) / gridDim.x;
     const int64_t r0 = blockIdx.x * per;
     const int64_t r1 = (r0 + per) < N ? (r0 + per) : N;
-    Pair mine{}; // the cost of this lane's points (lanes 0, 4, ..., 28)
+    Pair mine{}; // the cost of this lane's points
     for (int k0 = 0; k0 < K; k0 += TK) {
         const int tk = (K - k0) < TK ? (K - k0) : TK;
         for (int e = threadIdx.x; e < tk * d; e += blockDim.x)
@@ -437,23 +438,32 @@ __global__ void __launch_bounds__(kUpdThreads, 1)
         for (int e = threadIdx.x; e < tk; e += blockDim.x)
             cnt[e] = 0u;
         __syncthreads();
-        for (int64_t b = r0 + (int64_t)warp * kUpdRows; b < r1; b += (int64_t)nwarps * kUpdRows) {
-            const int nr = (r1 - b) < kUpdRows ? (int)(r1 - b) : kUpdRows;
+        for (int64_t b = r0 + (int64_t)warp * ROWS; b < r1; b += (int64_t)nwarps * ROWS) {
+            const int nr = (r1 - b) < ROWS ? (int)(r1 - b) : ROWS;
             const int my_label = lane < nr ? labels[b + lane] : 0;
-            float xv[kUpdRows][VEC];
+            // points of this batch to load: all on the first walk (for D^2),
+            // then only those whose centre is in the tile
+            // (on the first walk the row loads do not wait for the labels)
+            unsigned need = (1u << nr) - 1u;
+            if (k0 > 0) {
+                need = __ballot_sync(0xffffffffu, lane < nr && my_label >= k0 && my_label < k0 + tk);
+                if (need == 0)
+                    continue;
+            }
+            float xv[ROWS][VEC];
 #pragma unroll
-            for (int q = 0; q < kUpdRows; ++q)
+            for (int q = 0; q < ROWS; ++q)
 #pragma unroll
                 for (int t = 0; t < VEC; ++t) {
                     const int j = lane + 32 * t;
-                    xv[q][t] = (q < nr && j < d) ? x[(b + q) * d + j] : 0.f;
+                    xv[q][t] = (((need >> q) & 1u) && j < d) ? x[(b + q) * d + j] : 0.f;
                 }
             if (k0 == 0) {
                 // the assigned centres' features, all in flight, then the
-                // per-lane partial squared distances of the 8 points
-                float part[kUpdRows];
+                // per-lane partial squared distances of the batch's points
+                float part[ROWS];
 #pragma unroll
-                for (int q = 0; q < kUpdRows; ++q) {
+                for (int q = 0; q < ROWS; ++q) {
                     const int k = __shfl_sync(0xffffffffu, my_label, q);
                     float a0 = 0.f, a1 = 0.f;
 #pragma unroll
@@ -468,12 +478,12 @@ __global__ void __launch_bounds__(kUpdThreads, 1)
                     }
                     part[q] = a0 + a1;
                 }
-                // reduce-scatter: lane bits 4, 3, 2 select the point, bits 1, 0
-                // are summed last; lane 4r ends with point r's D^2
+                // reduce-scatter: lane bits 4, 3, ... select the point, the
+                // remaining low bits are summed last
 #pragma unroll
-                for (int h = 0; h < 3; ++h) {
-                    const int m = 16 >> h;     // 16, 8, 4
-                    const int w = 4 >> h;      // values kept: 4, 2, 1
+                for (int h = 0; h < kStages; ++h) {
+                    const int m = 16 >> h;          // 16, 8, 4 (, 2)
+                    const int w = (ROWS / 2) >> h;  // values kept
                     const bool up = (lane & m) != 0;
 #pragma unroll
                     for (int i = 0; i < w; ++i) {
@@ -483,17 +493,21 @@ __global__ void __launch_bounds__(kUpdThreads, 1)
                     }
                 }
                 float v = part[0];
-                v += __shfl_xor_sync(0xffffffffu, v, 2);
-                v += __shfl_xor_sync(0xffffffffu, v, 1);
-                const int r = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
-                if ((lane & 3) == 0 && r < nr) {
+#pragma unroll
+                for (int o = (16 >> kStages); o >= 1; o >>= 1)
+                    v += __shfl_xor_sync(0xffffffffu, v, o);
+                int r = 0;
+#pragma unroll
+                for (int h = 0; h < kStages; ++h)
+                    r |= ((lane >> (4 - h)) & 1) << (kStages - 1 - h);
+                if ((lane & ((32 / ROWS) - 1)) == 0 && r < nr) {
                     if (d2_out)
                         d2_out[b + r] = v;
                     mine.add(v);
                 }
             }
 #pragma unroll
-            for (int q = 0; q < kUpdRows; ++q) {
+            for (int q = 0; q < ROWS; ++q) {
                 if (q >= nr)
                     break;
                 const int k = __shfl_sync(0xffffffffu, my_label, q);
@@ -540,10 +554,10 @@ using UpdateFn = void (*)(const float *, int64_t, int, int, const float *, const
 UpdateFn update_fn(int d)
 {
     if (d <= 32)
-        return &lloyd_update_kernel<1>;
+        return &lloyd_update_kernel<1, 16>;
     if (d <= 64)
-        return &lloyd_update_kernel<2>;
-    return &lloyd_update_kernel<4>;
+        return &lloyd_update_kernel<2, 16>;
+    return &lloyd_update_kernel<4, 8>;
 }
 
 __global__ void lloyd_finalize_kernel(const float *c_in, int K, int d, const double *sums,
