@@ -360,9 +360,11 @@ KPP_API kpp_status kpp_lloyd_step(const float *points, int64_t N, int32_t d,
  * Distances are the FP32 difference form.  The nearest new candidate of a
  * point is searched on the tensor cores (the assignment of kpp_lloyd_step,
  * same near-tie bound) and its distance then taken exactly; the recluster
- * runs in one CTA.  The call synchronises `stream` once per round (the
- * number of new candidates sizes the next launches) and at the end, and
- * returns the device status: KPP_OK, KPP_ERR_DEGENERATE (fewer than K
+ * runs on one thread-block cluster.  The rounds keep their state on the
+ * device; the call synchronises `stream` after the rounds (the number of
+ * candidates sizes the recluster) and at the end -- and, only if a round drew
+ * more than 4096 candidates, runs the rounds again synchronising once per
+ * round -- and returns the device status: KPP_OK, KPP_ERR_DEGENERATE (fewer than K
  * candidates carry weight), KPP_ERR_TIMEOUT, or KPP_ERR_CAPACITY (more than
  * cand_cap candidates; nothing past the last whole round is written).
  */

@@ -55,6 +55,14 @@ bool tuned_options(int64_t N, int32_t d, int32_t K, int dt, const kpp_options &a
 
 namespace kpp {
 
+// kpp_lloyd_assign for centres whose first row and count are known only on
+// the device: rows [*row0, *row0 + *kdev) of `centres` (*kdev <= kmax; 0 is
+// a no-op), for points prepared by kpp_lloyd_prepare(..., kmax, ...).
+kpp_status lloyd_assign_device_count(const float *centres, const long long *row0,
+                                     const int32_t *kdev, int32_t kmax, int64_t N, int32_t d,
+                                     int32_t *labels_out, void *workspace, size_t workspace_bytes,
+                                     cudaStream_t stream);
+
 cudaError_t quantize_bf16(const float *x, int64_t n, uint16_t *out, cudaStream_t stream);
 cudaError_t quantize_fp8(const float *x, int64_t N, int d, uint8_t *q, float *scales,
                          cudaStream_t stream);

@@ -30,6 +30,7 @@
 
 #include "kpp.h"
 #include "kpp_device.cuh"
+#include "kpp_internal.h"
 
 namespace kpp {
 namespace {
@@ -46,11 +47,18 @@ constexpr size_t kAlign = 256;
 
 size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
+// Round state on the device (the rounds run without host round trips).
 struct Scalars {
     double phi;
-    long long count; // new candidates of the current round
-    long long pad_[30];
+    long long count;   // new candidates of the current round (0 after a stop)
+    long long nc;      // candidates so far
+    long long base;    // position of the current round's first candidate
+    long long max_new; // largest round drawn
+    int32_t n_chunk;   // min(count, candidates per assignment launch)
+    int32_t stop;      // the candidates outgrew their room: no further rounds
+    long long pad_[26];
 };
+static_assert(sizeof(Scalars) == 256, "round state is 256 bytes");
 
 struct Layout {
     int64_t range; // points per CTA
@@ -160,7 +168,8 @@ __global__ void __launch_bounds__(kThreads) kmpar_init_kernel(const float *x, in
                                                               int64_t range, uint64_t seed,
                                                               uint64_t stream, float *D2,
                                                               int32_t *lab, int64_t *cand,
-                                                              float *cbuf, Pair *part)
+                                                              float *cbuf, Pair *part,
+                                                              Scalars *sc)
 {
     __shared__ float c[kMaxD];
     __shared__ Pair sh[kThreads / 32];
@@ -170,8 +179,10 @@ __global__ void __launch_bounds__(kThreads) kmpar_init_kernel(const float *x, in
     for (int j = threadIdx.x; j < d; j += blockDim.x)
         c[j] = x[c0 * d + j];
     if (blockIdx.x == 0) {
-        if (threadIdx.x == 0)
+        if (threadIdx.x == 0) {
             cand[0] = c0;
+            sc->nc = 1;
+        }
         for (int j = threadIdx.x; j < d; j += blockDim.x)
             cbuf[j] = x[c0 * d + j];
     }
@@ -268,8 +279,12 @@ __global__ void __launch_bounds__(kThreads)
 }
 
 // Step 2b: exclusive scan of the per-CTA counts (one CTA of kGrid threads).
+// Also advances the round state: the round's count and first position, the
+// candidates so far, and the stop (status KPP_ERR_CAPACITY) if they would
+// outgrow `cap`.
 __global__ void __launch_bounds__(kGrid) kmpar_scan_kernel(const long long *bcnt, long long *boff,
-                                                           Scalars *sc)
+                                                           Scalars *sc, long long cap, int kl,
+                                                           Control *ctl)
 {
     __shared__ long long ws[kGrid / 32];
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
@@ -294,22 +309,38 @@ __global__ void __launch_bounds__(kGrid) kmpar_scan_kernel(const long long *bcnt
                 wi += y;
         }
         ws[lane] = wi - w;
-        if (lane == 31)
-            sc->count = wi;
+        if (lane == 31) {
+            long long cnt = sc->stop ? 0 : wi;
+            if (cnt > 0 && sc->nc + cnt > cap) {
+                sc->stop = 1;
+                cnt = 0;
+                atomicCAS(&ctl->status, KPP_OK, KPP_ERR_CAPACITY);
+            }
+            sc->count = cnt;
+            sc->base = sc->nc;
+            sc->nc += cnt;
+            sc->n_chunk = (int32_t)(cnt < kl ? cnt : kl);
+            if (wi > sc->max_new)
+                sc->max_new = wi;
+        }
     }
     __syncthreads();
     boff[t] = ws[warp] + inc - v;
 }
 
 // Step 2c: ordered compaction.  The round's candidates go to positions
-// base + (chosen points before them); each takes D^2 = 0 and its own
-// position as nearest candidate (a point is at distance 0 from itself).
+// base + (chosen points before them) (base and count from the round state);
+// each takes D^2 = 0 and its own position as nearest candidate (a point is
+// at distance 0 from itself).
 __global__ void __launch_bounds__(kThreads)
     kmpar_compact_kernel(const float *x, int64_t N, int d, int64_t range, const uint8_t *flags,
-                         const long long *boff, int64_t base, int64_t *cand, float *cbuf,
+                         const long long *boff, const Scalars *sc, int64_t *cand, float *cbuf,
                          float *D2, int32_t *lab)
 {
     __shared__ int wc[kThreads / 32 + 1];
+    if (sc->count == 0)
+        return;
+    const int64_t base = sc->base;
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5, nw = blockDim.x >> 5;
     const int64_t lo = blockIdx.x * range, hi = lo + range < N ? lo + range : N;
     int64_t pos0 = base + boff[blockIdx.x];
@@ -345,14 +376,20 @@ __global__ void __launch_bounds__(kThreads)
 
 // Step 2d: D^2 = min(D^2, exact distance to the candidate the tensor-core
 // assignment picked among cbuf[base .. base + n)); a tie goes to the earlier
-// position.  Writes the CTA's FP64 sum of the resulting D^2.
+// position.  Writes the CTA's sum of the resulting D^2 (an FP32 pair).
 template <int VEC>
 __global__ void __launch_bounds__(kThreads)
     kmpar_min_update_kernel(const float *x, int64_t N, int d, int64_t range, const float *cbuf,
-                            int64_t base, int32_t n, const int32_t *pick, float *D2, int32_t *lab,
-                            Pair *part)
+                            const Scalars *sc, int64_t c0, int kl, const int32_t *pick, float *D2,
+                            int32_t *lab, Pair *part)
 {
     __shared__ Pair sh[kThreads / 32];
+    // chunk c0 of the round: candidates base + c0 .. base + c0 + n - 1
+    const long long left = sc->count - c0;
+    const int32_t n = (int32_t)(left < kl ? left : kl);
+    if (n <= 0)
+        return; // D^2 unchanged: the CTA partials of the last update stand
+    const int64_t base = sc->base + c0;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     const int64_t lo = blockIdx.x * range, hi = lo + range < N ? lo + range : N;
     constexpr int kRowsInFlight = rows_in_flight<VEC>();
@@ -807,56 +844,88 @@ kpp_status kpp_kmeans_par(const float *points, int64_t N, int32_t d, int32_t K, 
     const int kl = lloyd_k(N);
     auto launched = [] { return cudaGetLastError() == cudaSuccess; };
 
-    // both status words (this call's and the assignment's) start at KPP_OK
-    if (cudaMemsetAsync(ws, 0, sizeof(Control), s) != cudaSuccess ||
-        cudaMemsetAsync(lws, 0, sizeof(Control), s) != cudaSuccess)
-        return KPP_ERR_CUDA;
-    kpp_status st = kpp_lloyd_prepare(points, N, d, kl, lws, L.lloyd_bytes, stream);
-    if (st != KPP_OK)
-        return st;
     auto init_fn = d <= 32 ? &kmpar_init_kernel<1> : d <= 64 ? &kmpar_init_kernel<2>
                                                              : &kmpar_init_kernel<4>;
     auto update_fn = d <= 32 ? &kmpar_min_update_kernel<1>
                              : d <= 64 ? &kmpar_min_update_kernel<2> : &kmpar_min_update_kernel<4>;
-    init_fn<<<kGrid, kThreads, 0, s>>>(points, N, d, L.range, seed, stream_id, D2, lab, cand_out,
-                                       cbuf, part);
-    kmpar_phi_kernel<<<1, 32, 0, s>>>(part, kGrid, sc);
-    if (!launched())
-        return KPP_ERR_LAUNCH;
-    int64_t nc = 1;
-    for (int r = 0; r < rounds; ++r) {
+    kpp_status st = kpp_lloyd_prepare(points, N, d, kl, lws, L.lloyd_bytes, stream);
+    if (st != KPP_OK)
+        return st;
+    // c_0, D^2 to it and phi, with both status words (this call's and the
+    // assignment's) and the round state cleared
+    auto start = [&]() -> kpp_status {
+        if (cudaMemsetAsync(ws, 0, sizeof(Control), s) != cudaSuccess ||
+            cudaMemsetAsync(lws, 0, sizeof(Control), s) != cudaSuccess ||
+            cudaMemsetAsync(sc, 0, sizeof(Scalars), s) != cudaSuccess)
+            return KPP_ERR_CUDA;
+        init_fn<<<kGrid, kThreads, 0, s>>>(points, N, d, L.range, seed, stream_id, D2, lab,
+                                           cand_out, cbuf, part, sc);
+        kmpar_phi_kernel<<<1, 32, 0, s>>>(part, kGrid, sc);
+        return launched() ? KPP_OK : KPP_ERR_LAUNCH;
+    };
+    auto draw = [&](int r) {
         kmpar_sample_kernel<<<kGrid, kThreads, 0, s>>>(D2, N, L.range, sc, ell, seed, stream_id, r,
                                                        flags, bcnt);
-        kmpar_scan_kernel<<<1, kGrid, 0, s>>>(bcnt, boff, sc);
-        if (!launched())
-            return KPP_ERR_LAUNCH;
-        long long n_new = 0;
-        if (cudaMemcpyAsync(&n_new, &sc->count, sizeof(n_new), cudaMemcpyDeviceToHost, s) !=
-                cudaSuccess ||
-            cudaStreamSynchronize(s) != cudaSuccess)
-            return KPP_ERR_CUDA;
-        if (nc + n_new > L.cap) {
-            *n_cand_out = nc;
-            return KPP_ERR_CAPACITY;
-        }
-        if (n_new == 0)
-            continue;
-        kmpar_compact_kernel<<<kGrid, kThreads, 0, s>>>(points, N, d, L.range, flags, boff, nc,
+        kmpar_scan_kernel<<<1, kGrid, 0, s>>>(bcnt, boff, sc, L.cap, kl, ctl);
+        kmpar_compact_kernel<<<kGrid, kThreads, 0, s>>>(points, N, d, L.range, flags, boff, sc,
                                                         cand_out, cbuf, D2, lab);
-        if (!launched())
-            return KPP_ERR_LAUNCH;
-        for (int64_t c0 = 0; c0 < n_new; c0 += kl) {
-            const int kc = (int)(n_new - c0 < kl ? n_new - c0 : kl);
-            st = kpp_lloyd_assign(cbuf + (nc + c0) * d, N, d, kc, pick, lws, L.lloyd_bytes, stream);
-            if (st != KPP_OK)
-                return st;
-            update_fn<<<kGrid, kThreads, 0, s>>>(points, N, d, L.range, cbuf, nc + c0, kc, pick,
-                                                 D2, lab, part);
-        }
+    };
+    Scalars hs;
+    auto read_state = [&]() -> bool {
+        return cudaMemcpyAsync(&hs, sc, sizeof(Scalars), cudaMemcpyDeviceToHost, s) ==
+                   cudaSuccess &&
+               cudaStreamSynchronize(s) == cudaSuccess;
+    };
+
+    // The rounds with their state on the device and no host round trip: each
+    // round's first kl new candidates are searched (the count is read by the
+    // kernels).  If a round drew more than kl, the rounds run again below with
+    // the count read on the host each round and one search per kl chunk.
+    if ((st = start()) != KPP_OK)
+        return st;
+    for (int r = 0; r < rounds; ++r) {
+        draw(r);
+        st = lloyd_assign_device_count(cbuf, &sc->base, &sc->n_chunk, kl, N, d, pick, lws,
+                                       L.lloyd_bytes, s);
+        if (st != KPP_OK)
+            return st;
+        update_fn<<<kGrid, kThreads, 0, s>>>(points, N, d, L.range, cbuf, sc, 0, kl, pick, D2, lab,
+                                             part);
         kmpar_phi_kernel<<<1, 32, 0, s>>>(part, kGrid, sc);
         if (!launched())
             return KPP_ERR_LAUNCH;
-        nc += n_new;
+    }
+    if (!read_state())
+        return KPP_ERR_CUDA;
+    if (hs.max_new > kl) {
+        if ((st = start()) != KPP_OK)
+            return st;
+        for (int r = 0; r < rounds; ++r) {
+            draw(r);
+            if (!launched() || !read_state())
+                return KPP_ERR_CUDA;
+            if (hs.stop)
+                break;
+            for (int64_t c0 = 0; c0 < hs.count; c0 += kl) {
+                const int kc = (int)(hs.count - c0 < kl ? hs.count - c0 : kl);
+                st = kpp_lloyd_assign(cbuf + (hs.base + c0) * d, N, d, kc, pick, lws,
+                                      L.lloyd_bytes, stream);
+                if (st != KPP_OK)
+                    return st;
+                update_fn<<<kGrid, kThreads, 0, s>>>(points, N, d, L.range, cbuf, sc, c0, kl, pick,
+                                                     D2, lab, part);
+            }
+            kmpar_phi_kernel<<<1, 32, 0, s>>>(part, kGrid, sc);
+            if (!launched())
+                return KPP_ERR_LAUNCH;
+        }
+        if (!read_state())
+            return KPP_ERR_CUDA;
+    }
+    const int64_t nc = hs.nc;
+    if (hs.stop) {
+        *n_cand_out = nc;
+        return KPP_ERR_CAPACITY;
     }
     *n_cand_out = nc;
     if (cudaMemsetAsync(wts, 0, (size_t)nc * 8, s) != cudaSuccess)

@@ -93,8 +93,8 @@ __device__ __forceinline__ void split_bf16(float v, __nv_bfloat16 &hi, __nv_bflo
 
 // A thread per (row, group of 8 features): eight FP32 loads, one 16-byte
 // store per plane.  dp / 8 is 8 or 16, so the indexing is shifts and masks.
-__global__ void split_rows_kernel(const float *x, int64_t rows, int d, int dp, __nv_bfloat16 *hi,
-                                  __nv_bfloat16 *lo)
+__device__ __forceinline__ void split_rows_body(const float *x, int64_t rows, int d, int dp,
+                                                __nv_bfloat16 *hi, __nv_bfloat16 *lo)
 {
     const int sh = dp == 64 ? 3 : 4;
     const int64_t n = rows << sh;
@@ -113,16 +113,43 @@ __global__ void split_rows_kernel(const float *x, int64_t rows, int d, int dp, _
     }
 }
 
-// |c_k|^2 in FP32 (one thread per centre)
-__global__ void centre_norms_kernel(const float *c, int K, int d, float *cn)
+__global__ void split_rows_kernel(const float *x, int64_t rows, int d, int dp, __nv_bfloat16 *hi,
+                                  __nv_bfloat16 *lo)
 {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= K)
-        return;
+    split_rows_body(x, rows, d, dp, hi, lo);
+}
+
+// The same for rows [*row0, *row0 + *rows) of `base`, counts read on the device.
+__global__ void split_rows_dev_kernel(const float *base, const long long *row0,
+                                      const int32_t *rows, int d, int dp, __nv_bfloat16 *hi,
+                                      __nv_bfloat16 *lo)
+{
+    split_rows_body(base + *row0 * d, *rows, d, dp, hi, lo);
+}
+
+// |c_k|^2 in FP32 (one thread per centre); the device-count form reads K and
+// the first row from device memory.
+__device__ __forceinline__ void centre_norm(const float *c, int k, int d, float *cn)
+{
     float s = 0.f;
     for (int j = 0; j < d; ++j)
         s = fmaf(c[(int64_t)k * d + j], c[(int64_t)k * d + j], s);
     cn[k] = s;
+}
+
+__global__ void centre_norms_kernel(const float *c, int K, int d, float *cn)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < K)
+        centre_norm(c, k, d, cn);
+}
+
+__global__ void centre_norms_dev_kernel(const float *base, const long long *row0,
+                                        const int32_t *K, int d, float *cn)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < *K)
+        centre_norm(base + *row0 * d, k, d, cn);
 }
 
 // ---------------------------------------------------------------------------
@@ -131,6 +158,7 @@ __global__ void centre_norms_kernel(const float *c, int K, int d, float *cn)
 struct AssignArgs {
     int64_t N;
     int32_t K;
+    const int32_t *Kdev; // if set, K is read here (written by an earlier launch)
     int32_t nk;     // feature chunks (dp / 64)
     int32_t stages; // centre-tile stages in shared memory
     int32_t abufs;  // point-tile buffers (2: the next group's load overlaps this one)
@@ -163,6 +191,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                         const __grid_constant__ CUtensorMap map_clo, AssignArgs a)
 {
     using namespace tc;
+    const int K = a.Kdev ? *a.Kdev : a.K;
+    if (K <= 0)
+        return; // nothing to assign (every thread leaves before any setup)
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                                 ~uintptr_t(1023));
@@ -199,9 +230,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     // centre norms, padded with +infinity up to whole centre tiles (those
     // columns can never win)
-    const int n_ct = (a.K + kBN - 1) / kBN;
+    const int n_ct = (K + kBN - 1) / kBN;
     for (int k = threadIdx.x; k < n_ct * kBN; k += blockDim.x)
-        s_cn[k] = k < a.K ? a.cn[k] : __int_as_float(0x7f800000);
+        s_cn[k] = k < K ? a.cn[k] : __int_as_float(0x7f800000);
     if (warp == 2)
         tmem_alloc(&tmem_base, kTmemCols);
     fence_before_sync();
@@ -648,7 +679,78 @@ int sm_count()
     return sms;
 }
 
+// The assignment of N prepared points to K centres.  With row0 and kdev set,
+// the centres are rows [*row0, *row0 + *kdev) of `centres` and K is only the
+// largest count the launch is sized for; both are read on the device.
+kpp_status assign_impl(const float *centres, const long long *row0, const int32_t *kdev, int32_t K,
+                       int64_t N, int32_t d, int32_t *labels_out, void *workspace,
+                       size_t workspace_bytes, cudaStream_t s)
+{
+    const Layout L = layout(N, d, K);
+    if (!workspace || (reinterpret_cast<uintptr_t>(workspace) % kAlign) != 0 ||
+        workspace_bytes < L.bytes)
+        return KPP_ERR_WORKSPACE;
+    char *ws = reinterpret_cast<char *>(workspace);
+    const int sms = sm_count();
+    if (sms <= 0)
+        return KPP_ERR_CUDA;
+    auto *phi = reinterpret_cast<__nv_bfloat16 *>(ws + L.off_phi);
+    auto *plo = reinterpret_cast<__nv_bfloat16 *>(ws + L.off_plo);
+    auto *chi = reinterpret_cast<__nv_bfloat16 *>(ws + L.off_chi);
+    auto *clo = reinterpret_cast<__nv_bfloat16 *>(ws + L.off_clo);
+    float *cn = reinterpret_cast<float *>(ws + L.off_cn);
+    CUtensorMap m_phi, m_plo, m_chi, m_clo;
+    if (!make_map(&m_phi, phi, N, L.dp, kBM) || !make_map(&m_plo, plo, N, L.dp, kBM) ||
+        !make_map(&m_chi, chi, K, L.dp, kBN) || !make_map(&m_clo, clo, K, L.dp, kBN))
+        return KPP_ERR_CUDA;
+    const int nk = L.dp / kBK;
+    const size_t smem = assign_smem(nk, K);
+    if (cudaFuncSetAttribute(lloyd_assign_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess)
+        return KPP_ERR_CUDA;
+    AssignArgs a;
+    a.N = N;
+    a.K = K;
+    a.Kdev = kdev;
+    a.nk = nk;
+    a.abufs = assign_abufs(nk, K);
+    a.stages = assign_stages(nk, K, a.abufs);
+    a.cn = cn;
+    a.labels = labels_out;
+    a.ctl = reinterpret_cast<Control *>(ws);
+    a.timeout_ns = 2000000000ull;
+    if (a.stages < 2)
+        return KPP_ERR_UNSUPPORTED;
+    if (cudaMemsetAsync(ws, 0, sizeof(Control), s) != cudaSuccess)
+        return KPP_ERR_CUDA;
+    if (kdev) {
+        split_rows_dev_kernel<<<(K * L.dp / 8 + 255) / 256, 256, 0, s>>>(centres, row0, kdev, d,
+                                                                         L.dp, chi, clo);
+        centre_norms_dev_kernel<<<(K + 127) / 128, 128, 0, s>>>(centres, row0, kdev, d, cn);
+    } else {
+        split_rows_kernel<<<(K * L.dp / 8 + 255) / 256, 256, 0, s>>>(centres, K, d, L.dp, chi,
+                                                                     clo);
+        centre_norms_kernel<<<(K + 127) / 128, 128, 0, s>>>(centres, K, d, cn);
+    }
+    const int64_t n_grp = ((N + kBM - 1) / kBM + kMT - 1) / kMT;
+    const int grid = (int)(n_grp < sms ? n_grp : sms);
+    lloyd_assign_kernel<<<grid, kThreads, smem, s>>>(m_phi, m_plo, m_chi, m_clo, a);
+    return cudaGetLastError() == cudaSuccess ? KPP_OK : KPP_ERR_LAUNCH;
+}
+
 } // namespace
+
+kpp_status lloyd_assign_device_count(const float *centres, const long long *row0,
+                                     const int32_t *kdev, int32_t kmax, int64_t N, int32_t d,
+                                     int32_t *labels_out, void *workspace, size_t workspace_bytes,
+                                     cudaStream_t stream)
+{
+    if (!centres || !row0 || !kdev || !labels_out || !shape_ok(N, d, kmax))
+        return KPP_ERR_INVALID_ARG;
+    return assign_impl(centres, row0, kdev, kmax, N, d, labels_out, workspace, workspace_bytes,
+                       stream);
+}
+
 } // namespace kpp
 
 using namespace kpp;
@@ -688,49 +790,8 @@ kpp_status kpp_lloyd_assign(const float *centres, int64_t N, int32_t d, int32_t 
 {
     if (!centres || !labels_out || !shape_ok(N, d, K))
         return KPP_ERR_INVALID_ARG;
-    const Layout L = layout(N, d, K);
-    if (!workspace || (reinterpret_cast<uintptr_t>(workspace) % kAlign) != 0 ||
-        workspace_bytes < L.bytes)
-        return KPP_ERR_WORKSPACE;
-    char *ws = reinterpret_cast<char *>(workspace);
-    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    const int sms = sm_count();
-    if (sms <= 0)
-        return KPP_ERR_CUDA;
-    auto *phi = reinterpret_cast<__nv_bfloat16 *>(ws + L.off_phi);
-    auto *plo = reinterpret_cast<__nv_bfloat16 *>(ws + L.off_plo);
-    auto *chi = reinterpret_cast<__nv_bfloat16 *>(ws + L.off_chi);
-    auto *clo = reinterpret_cast<__nv_bfloat16 *>(ws + L.off_clo);
-    float *cn = reinterpret_cast<float *>(ws + L.off_cn);
-    CUtensorMap m_phi, m_plo, m_chi, m_clo;
-    if (!make_map(&m_phi, phi, N, L.dp, kBM) || !make_map(&m_plo, plo, N, L.dp, kBM) ||
-        !make_map(&m_chi, chi, K, L.dp, kBN) || !make_map(&m_clo, clo, K, L.dp, kBN))
-        return KPP_ERR_CUDA;
-    const int nk = L.dp / kBK;
-    const size_t smem = assign_smem(nk, K);
-    if (cudaFuncSetAttribute(lloyd_assign_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem) != cudaSuccess)
-        return KPP_ERR_CUDA;
-    AssignArgs a;
-    a.N = N;
-    a.K = K;
-    a.nk = nk;
-    a.abufs = assign_abufs(nk, K);
-    a.stages = assign_stages(nk, K, a.abufs);
-    a.cn = cn;
-    a.labels = labels_out;
-    a.ctl = reinterpret_cast<Control *>(ws);
-    a.timeout_ns = 2000000000ull;
-    if (a.stages < 2)
-        return KPP_ERR_UNSUPPORTED;
-    if (cudaMemsetAsync(ws, 0, sizeof(Control), s) != cudaSuccess)
-        return KPP_ERR_CUDA;
-    split_rows_kernel<<<(K * L.dp / 8 + 255) / 256, 256, 0, s>>>(centres, K, d, L.dp, chi, clo);
-    centre_norms_kernel<<<(K + 127) / 128, 128, 0, s>>>(centres, K, d, cn);
-    const int64_t n_grp = ((N + kBM - 1) / kBM + kMT - 1) / kMT;
-    const int grid = (int)(n_grp < sms ? n_grp : sms);
-    lloyd_assign_kernel<<<grid, kThreads, smem, s>>>(m_phi, m_plo, m_chi, m_clo, a);
-    return cudaGetLastError() == cudaSuccess ? KPP_OK : KPP_ERR_LAUNCH;
+    return assign_impl(centres, nullptr, nullptr, K, N, d, labels_out, workspace, workspace_bytes,
+                       reinterpret_cast<cudaStream_t>(stream));
 }
 
 kpp_status kpp_lloyd_step(const float *points, int64_t N, int32_t d, const float *centres,
