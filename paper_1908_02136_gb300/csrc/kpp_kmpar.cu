@@ -26,8 +26,6 @@
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
-#include <cstring>
-
 #include "kpp.h"
 #include "kpp_device.cuh"
 #include "kpp_internal.h"
@@ -39,7 +37,7 @@ constexpr int kThreads = 256;      // per-point kernels
 constexpr int kGrid = 1024;        // their CTAs; each owns a contiguous range of points
 constexpr int kChunk = 4096;       // candidates per tensor-core assignment (its K limit)
 constexpr int kMaxD = 128;
-constexpr int kRecThreads = 1024;  // recluster CTA
+constexpr int kRecThreads = 1024;  // most threads per recluster CTA
 // rows a warp loads before reducing, by features per lane (VEC = ceil(d/32)):
 // 16 rows of one or two registers, 8 of four (<= 32: lane q owns row q)
 template <int VEC> __host__ __device__ constexpr int rows_in_flight() { return VEC == 4 ? 8 : 16; }
