@@ -235,11 +235,92 @@ def oracle_sample_passes(wl):
     return max(1, min(wl.K, int(15.0 / max(per_pass, 1e-9))))
 
 
+def _reference_line(args, world, metric, value, ms, config, sample):
+    cores, model = cpu_info()
+    print(json.dumps({
+        "impl": "reference", "metric": metric, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": config,
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": sample, "host_cores": cores, "cpu": model},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def run_reference_other(args, world):
+    """The reference arm of the batch, Lloyd and k-means|| workloads: the
+    oracle's routine for that step on a bounded sample, N*K*d per second."""
+    import numpy as np
+
+    import oracle
+    from paper_1908_02136_gb300 import datagen
+
+    steps = max(1, args.steps)
+    if args.workload == BATCH_WORKLOAD:
+        probs, budget = [], 0.0
+        for pr in datagen.batch_table():
+            if budget + pr.N * pr.K * pr.d > 2e9:
+                continue
+            probs.append(pr)
+            budget += pr.N * pr.K * pr.d
+        data = [(pr, datagen.batch_problem_points(pr)) for pr in probs]
+        times = []
+        for s_ in range(args.warmup + steps):
+            t0 = time.perf_counter()
+            for pr, x in data:
+                oracle.seed(x, pr.K, 1, pr.p)
+            if s_ >= args.warmup:
+                times.append(time.perf_counter() - t0)
+        dt = sum(times) / len(times)
+        _reference_line(args, world, METRIC, budget / dt, 1e3 * dt,
+                        {"workload": BATCH_WORKLOAD, "problems": len(probs)},
+                        f"{len(probs)} of the 512 problems (N*K*d <= 2e9 in total), "
+                        "one oracle seeding each per step (serial FP64)")
+        return
+    lloyd = args.workload.startswith(LLOYD_PREFIX)
+    wl = datagen.WORKLOADS[args.workload[len(LLOYD_PREFIX if lloyd else KMPAR_PREFIX):]]
+    N, d, K = wl.N, wl.d, wl.K
+    if lloyd:
+        n_s = int(max(K, min(N, 3e9 / (K * d))))
+    else:
+        ell, R = args.ell_mult * K, args.rounds
+        n_s = int(min(N, max(4 * K, 3e9 / (ell * R * d))))
+    x = datagen.gmm(n_s, d, wl.n_comp, wl.data_seed, wl.mean_box, wl.sigma, wl.weights,
+                    wl.outlier_frac)
+    C = x[:K].astype(np.float64)
+    times = []
+    for s_ in range(args.warmup + steps):
+        t0 = time.perf_counter()
+        if lloyd:
+            oracle.lloyd_step(x, C)
+        else:
+            oracle.kmeans_par(x, K, ell, R, wl.draw_seed, 0, cand_cap=n_s)
+        if s_ >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    dt = sum(times) / len(times)
+    if lloyd:
+        metric = "k-means Lloyd iteration N*K*d/s (after k-means++ seeding)"
+        sample = (f"one Lloyd step of the first {n_s} of {N} points from {K} centres "
+                  "(the sample's first points) per step (serial FP64)")
+    else:
+        metric = "k-means|| initialisation N*K*d/s (oversampling + weighted recluster)"
+        sample = (f"k-means|| on {n_s} of {N} points (same K, ell, rounds) per step "
+                  "(serial FP64)")
+    _reference_line(args, world, metric, n_s * K * d / dt, 1e3 * dt,
+                    {"workload": args.workload, "N": N, "d": d, "K": K, "sample_points": n_s},
+                    sample)
+
+
 def run_reference(args, rank, world):
     """--impl reference: the FP64 CPU oracle as it stands, on the host cores."""
     from paper_1908_02136_gb300 import datagen
 
     if rank != 0:
+        return
+    if (args.workload == BATCH_WORKLOAD or args.workload.startswith(LLOYD_PREFIX)
+            or args.workload.startswith(KMPAR_PREFIX)):
+        run_reference_other(args, world)
         return
     wl = datagen.WORKLOADS[args.workload]
     import numpy as np
