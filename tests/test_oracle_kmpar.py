@@ -142,3 +142,32 @@ def test_kmeans_par_covers_well_separated_clusters():
         assert np.all(np.diff(r["cand"][1:]) != 0)
         covered += len(set(lab[r["idx"]].tolist())) == 6
     assert covered >= 18
+
+
+def test_kmeans_par_is_its_steps_in_order():
+    # the end-to-end run against its steps wired here from the readings: P1
+    # first seed and D^2, P2 round r drawn at counter {i, r + 1} with the
+    # candidates appended in index order and D^2 / phi updated, P3 weights,
+    # P4 the weighted recluster at counters {m, 0, 1, 0}
+    x = datagen.gmm(700, 4, 5, seed=12)
+    K, ell, rounds, seed, stream = 5, 9.0, 4, 21, 3
+    r = oracle.kmeans_par(x, K, ell, rounds, seed, stream)
+    N = x.shape[0]
+    c0 = min(int(oracle.uniform(seed, stream, 0) * N), N - 1)
+    cand = [c0]
+    D2, phi = oracle.min_update(x, [c0])
+    for rr in range(rounds):
+        flags, p, u = oracle.kmpar_select(D2, phi, ell, seed, stream, rr)
+        # the draws are Philox at counter {i, r + 1, 0, 0}
+        for i in (0, N // 2, N - 1):
+            assert u[i] == oracle.uniform_ctr(seed, stream, i, rr + 1, 0, 0)
+        new = np.flatnonzero(flags)
+        cand.extend(new.tolist())
+        if new.size:
+            D2, phi = oracle.min_update(x, new, D2)
+    assert np.array_equal(r["cand"], np.array(cand))
+    w = oracle.kmpar_weights(x, cand)
+    assert np.array_equal(r["w"], w)
+    pos, own, st = oracle.weighted_seed(x, cand, w, K, seed, stream)
+    assert st == 0
+    assert np.array_equal(r["idx"], np.array(cand)[pos])
