@@ -39,8 +39,11 @@ constexpr int kChunk = 4096;       // candidates per tensor-core assignment (its
 constexpr int kMaxD = 128;
 constexpr int kRecThreads = 1024;  // most threads per recluster CTA
 // rows a warp loads before reducing, by features per lane (VEC = ceil(d/32)):
-// 16 rows of one or two registers, 8 of four (<= 32: lane q owns row q)
-template <int VEC> __host__ __device__ constexpr int rows_in_flight() { return VEC == 4 ? 8 : 16; }
+// 32 rows of one register, 16 of two, 8 of four (<= 32: lane q owns row q)
+template <int VEC> __host__ __device__ constexpr int rows_in_flight()
+{
+    return VEC == 1 ? 32 : VEC == 2 ? 16 : 8;
+}
 constexpr size_t kAlign = 256;
 
 size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
