@@ -8,6 +8,13 @@ each step is timed with CUDA events on the launching stream.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
                   [--dtype f32|bf16|fp8] [--impl kpp|reference]
 
+Workloads: the seeding workloads (default gmm-N1e6-d32-K256), ``batch-512``
+(kpp_seed_batched over 512 uneven problems), ``lloyd-<seeding workload>``
+(one Lloyd iteration from that workload's k-means++ seeds; the assignment is
+also timed alone for its tensor roofline) and ``kmpar-<seeding workload>``
+(one whole k-means|| initialisation, ell = --ell-mult x K, --rounds rounds;
+its nearest-candidate search timed alone for the roofline).
+
 Under torchrun (N > 1), with no collective on the data path: for a single
 problem every rank seeds its own replica of the workload (its own Philox
 stream): weak scaling; for the 512-problem batch the problems are split
