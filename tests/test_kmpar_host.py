@@ -49,3 +49,15 @@ def test_tensor_helper_rejects_host_tensors():
         kpp.kmeans_par(torch.zeros((10, 4)), 2, 1)
     with pytest.raises(ValueError):
         kpp.kmeans_par(torch.zeros(10), 2, 1)
+
+
+def test_no_cpu_fallback_anywhere():
+    # host tensors are refused before any work: there is no CPU path
+    torch = pytest.importorskip("torch")
+    x = torch.zeros((100, 4))
+    with pytest.raises(ValueError):
+        kpp.seed(x, 2, 1)
+    with pytest.raises(ValueError):
+        kpp.Lloyd(x, 2)
+    with pytest.raises(ValueError):
+        kpp.kmeans_par(x, 2, 1)
