@@ -42,7 +42,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "k-means++ seeding ms & N·K·d/s; HBM GB/s vs peak; BF16/batched vs FP32"
 UNIT = "N*K*d/s"
-DEFAULT_WORKLOAD = "gmm-N1e6-d32-K256"
+DEFAULT_WORKLOAD = "gmm-N2e7-d128-K2048-t3"
 BATCH_WORKLOAD = "batch-512"
 LLOYD_PREFIX = "lloyd-"  # e.g. lloyd-gmm-N1e7-d64-K1024: one Lloyd iteration from the seeds
 KMPAR_PREFIX = "kmpar-"  # e.g. kmpar-gmm-N1e6-d32-K256: k-means|| (ell = 2K, 5 rounds)
@@ -63,6 +63,13 @@ def parse():
     ap.add_argument("--alternate", type=int, default=0)
     ap.add_argument("--l2-policy", type=int, default=0)
     ap.add_argument("--min-rows", type=int, default=0)
+    ap.add_argument("--forms", default="bf16,fp8",
+                    help="FP32 runs: precision forms of the same data timed beside it "
+                         "(comma list, or 'none')")
+    ap.add_argument("--form-steps", type=int, default=3,
+                    help="timed steps of each precision form beside the FP32 run")
+    ap.add_argument("--no-read-peaks", action="store_true",
+                    help="skip the live pure-read bandwidth measurement")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-phi", action="store_true")
@@ -133,18 +140,21 @@ def _profile_fields(path: str, names) -> dict:
     return fields
 
 
-def profiled_traffic(kind: str, workload: str, dtype: str, plan: dict):
+def profiled_traffic(kind: str, workload: str, dtype: str, plan: dict, passes: int = 1):
     """DRAM bytes per launch from the committed ncu summary of this kernel on
-    this workload, or None if there is none, its launch shape differs or its
-    sources changed since."""
+    this workload (its per-pass figure times the passes of one launch), or
+    None if there is none, its launch shape differs or its sources changed
+    since."""
     path = os.path.join(ROOT, "profiles", f"{kind}_kernel_{workload}_{dtype}.md")
-    f = _profile_fields(path, ("traffic_bytes_per_launch", "kernel_source_sha256",
-                               "plan_signature"))
+    f = _profile_fields(path, ("traffic_bytes_per_pass", "traffic_bytes_per_launch",
+                               "kernel_source_sha256", "plan_signature"))
     if f.get("kernel_source_sha256") != kernel_source_hash(kind):
         return None
     if f.get("plan_signature") != plan_signature(plan):
         return None
     try:
+        if "traffic_bytes_per_pass" in f:
+            return int(float(f["traffic_bytes_per_pass"]) * passes)
         return int(f["traffic_bytes_per_launch"])
     except (KeyError, ValueError):
         return None
@@ -227,21 +237,6 @@ def cpu_info():
     return os.cpu_count(), model
 
 
-def time_oracle(points, wl, K_sample, seed, stream_id, scales=None):
-    """The FP64 oracle on the first K_sample passes of the workload."""
-    import oracle
-
-    t0 = time.perf_counter()
-    oracle.seed(points, K_sample, seed, stream_id, scales=scales)
-    return time.perf_counter() - t0
-
-
-def oracle_sample_passes(wl):
-    # about 10-30 s of serial FP64 work at ~1.5 ns per coordinate per pass
-    per_pass = wl.N * wl.d * 1.5e-9
-    return max(1, min(wl.K, int(15.0 / max(per_pass, 1e-9))))
-
-
 def _reference_line(args, world, metric, value, ms, config, sample):
     cores, model = cpu_info()
     print(json.dumps({
@@ -320,7 +315,8 @@ def run_reference_other(args, world):
 
 
 def run_reference(args, rank, world):
-    """--impl reference: the FP64 CPU oracle as it stands, on the host cores."""
+    """--impl reference: the FP64 CPU oracle as it stands, on the host cores
+    (the multi-threaded seeding oracle for the seeding workloads)."""
     from paper_1908_02136_gb300 import datagen
 
     if rank != 0:
@@ -330,31 +326,40 @@ def run_reference(args, rank, world):
         run_reference_other(args, world)
         return
     wl = datagen.WORKLOADS[args.workload]
-    import numpy as np
-
     import oracle
 
+    # the workload's recipe on at most 2*10^6 points (numpy draws the larger
+    # workloads too slowly for a bench run)
     x = datagen.workload_points(wl) if wl.N <= 2_000_000 else datagen.gmm(
         min(wl.N, 2_000_000), wl.d, wl.n_comp, wl.data_seed, wl.mean_box, wl.sigma, wl.weights,
         wl.outlier_frac)
     N = x.shape[0]
-    K_s = max(1, oracle_sample_passes(wl) // max(1, args.steps + args.warmup))
+    cores, model = cpu_info()
+    # passes per step sized so that warm-up and timed steps take about two minutes
+    t0 = time.perf_counter()
+    oracle.seed_mt(x, min(2, wl.K), wl.draw_seed, 0, threads=cores)
+    per_pass = (time.perf_counter() - t0) / min(2, wl.K)
+    budget = max(0.5, 120.0 / max(1, args.steps + args.warmup))
+    K_s = int(max(1, min(wl.K, budget / max(per_pass, 1e-9))))
     for _ in range(args.warmup):
-        oracle.seed(x[: min(N, 10_000)], 2, 1)
-    times = []
+        oracle.seed_mt(x, K_s, wl.draw_seed, 0, threads=cores)
+    times, threads = [], cores
     for s in range(args.steps):
-        times.append(time_oracle(x, wl, K_s, wl.draw_seed, s))
+        t0 = time.perf_counter()
+        r = oracle.seed_mt(x, K_s, wl.draw_seed, s, threads=cores)
+        times.append(time.perf_counter() - t0)
+        threads = r["threads"]
     ms = 1e3 * sum(times) / len(times)
     value = N * K_s * wl.d / (sum(times) / len(times))
-    cores, model = cpu_info()
-    sample = f"{N} points x {wl.d} dims, {K_s} of {wl.K} passes per step (serial FP64 oracle)"
+    sample = (f"{N} of {wl.N} points x {wl.d} dims (the workload's recipe), {K_s} of {wl.K} "
+              f"passes per step (multi-threaded FP64 oracle, {threads} threads)")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": {"workload": wl.name, "N": N, "d": wl.d, "K": wl.K,
                                         "dtype": "f32", "passes_per_step": K_s},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                          "sample": sample, "host_cores": cores, "cpu": model},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
@@ -757,6 +762,341 @@ def run_kmpar(args, rank, world, dev, pg, barrier):
         }), flush=True)
 
 
+def l2_bytes(dev) -> int:
+    import torch
+
+    try:
+        return int(torch.cuda.get_device_properties(dev).L2_cache_size)
+    except (AttributeError, RuntimeError):
+        return 126 << 20
+
+
+def read_peaks(kpp, dev):
+    """Pure-read bandwidth of this GPU measured live (kpp_measure_read): HBM
+    over a 4 GiB buffer, L2 over 64 MiB read 64 times after a warming sweep."""
+    import torch
+
+    out = {}
+    try:
+        out["hbm_read_gbs"] = kpp.measure_read_gbs(4 << 30, 8, dev)
+        out["l2_read_gbs"] = kpp.measure_read_gbs(64 << 20, 64, dev)
+    except (kpp.KppError, RuntimeError) as e:
+        out["error"] = str(e)
+    torch.cuda.synchronize(dev)
+    torch.cuda.empty_cache()
+    return out
+
+
+def roofline_for(plan, form_name, N, d, K, eb, has_scales, ms_per_step, wl_name, dtype, dev,
+                 peaks_live):
+    """Roofline of the dominant kernel of one seeding (the persistent kernel,
+    one launch per seeding, or the streamed pass kernel, K launches).
+
+    Algorithmic bytes per pass = the points (N*d*b, plus 4N for FP8 scales),
+    plus the 8N bytes of D^2 read and written where D^2 lives in global memory
+    (streamed form; persistent form without room for D^2 in shared memory).
+    The bound is L2 when that working set fits the L2 (the persistent form
+    keeps it there with an evict-last policy), HBM otherwise; `peak` is the
+    measured copy bandwidth of MEASURED_PEAKS.json for HBM and the live
+    L2 read rate for L2, with the live pure-read rates reported beside."""
+    peaks = measured_peaks()
+    hbm_copy = peaks["hbm_gbs"] if peaks else 6800.0
+    launches = plan["launches"]
+    per_launch_ms = ms_per_step / launches
+    passes_per_launch = K // launches
+    point_bytes = N * d * eb + (4 * N if has_scales else 0)
+    d2_global = form_name in ("streamed", "recompute") or not plan["d2_in_smem"]
+    d2_bytes = 8 * N if d2_global else 0
+    per_pass = point_bytes + d2_bytes
+    alg_bytes = passes_per_launch * per_pass
+    achieved = alg_bytes / (per_launch_ms / 1e3) / 1e9
+    working_set = point_bytes + (4 * N if d2_global else 0)
+    l2 = l2_bytes(dev)
+    in_l2 = working_set <= l2
+    traffic = (profiled_traffic(form_name, wl_name, dtype, plan, passes_per_launch)
+               if form_name in KERNEL_SOURCES else None)
+    if in_l2 and "l2_read_gbs" in peaks_live:
+        bound, peak, src = "l2", peaks_live["l2_read_gbs"], "measured live: L2 read (kpp_measure_read)"
+    else:
+        bound, peak = "hbm", hbm_copy
+        src = "measured copy (MEASURED_PEAKS.json)" if peaks else "fallback"
+    r = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "GB/s",
+         "frac": achieved / peak, "traffic": traffic, "peak_source": src,
+         "kernel": f"{form_name}_kernel", "algorithmic_bytes_per_launch": alg_bytes,
+         "algorithmic_bytes_per_pass": per_pass, "points_bytes_per_pass": point_bytes,
+         "working_set_bytes": working_set, "l2_bytes": l2,
+         "hbm_copy_gbs": hbm_copy, "frac_of_hbm_copy": achieved / hbm_copy}
+    if "hbm_read_gbs" in peaks_live:
+        r["hbm_read_gbs"] = peaks_live["hbm_read_gbs"]
+        r["frac_of_hbm_read"] = achieved / peaks_live["hbm_read_gbs"]
+    if "l2_read_gbs" in peaks_live:
+        r["l2_read_gbs"] = peaks_live["l2_read_gbs"]
+    if traffic is not None:
+        r["traffic_over_algorithmic"] = traffic / alg_bytes
+    return r
+
+
+def run_seeding(args, rank, world, local, dev, pg, barrier):
+    """One problem of a seeding workload: the FP32 (or --dtype) seeding timed
+    over --steps, then -- for an FP32 run -- the same data stored as BF16 and
+    FP8 (--forms), each timed on fewer steps, with the cost distortion of its
+    seeds; the end-to-end time through kpp_seed_host; the roofline of the
+    dominant kernel; and the multi-threaded FP64 oracle as the CPU baseline."""
+    import ctypes
+
+    import numpy as np
+    import torch
+
+    import paper_1908_02136_gb300 as kpp
+    from paper_1908_02136_gb300 import datagen, multi
+
+    wl = datagen.WORKLOADS[args.workload]
+    if args.n_points or args.k_seeds:
+        import dataclasses
+
+        n_, k_ = args.n_points or wl.N, args.k_seeds or wl.K
+        wl = dataclasses.replace(wl, N=n_, K=k_, name=f"{wl.name}@N{n_}K{k_}")
+    x_np = datagen.workload_points(wl) if wl.N <= 2_000_000 else None
+    x = torch.from_numpy(x_np).to(dev) if x_np is not None else datagen.workload_points(wl, dev)
+    N, d, K = wl.N, wl.d, wl.K
+    peaks_live = read_peaks(kpp, dev) if not args.no_read_peaks else {}
+    opts = kpp.Options()
+    opts.form = args.form
+    opts.lanes_per_row = args.lanes
+    opts.ctas_per_sm = args.ctas_per_sm
+    opts.smem_cache = args.smem_cache
+    opts.alternate = args.alternate
+    opts.l2_policy = args.l2_policy
+    opts.min_rows_per_cta = args.min_rows
+    knobs = (args.form, args.lanes, args.ctas_per_sm, args.smem_cache, args.alternate,
+             args.l2_policy, args.min_rows)
+    stream = torch.cuda.Stream(dev)
+    sh = ctypes.c_void_p(stream.cuda_stream)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    seed = wl.draw_seed
+    stream_id = multi.replica_stream(0, rank)
+    codes = {"f32": kpp.F32, "bf16": kpp.BF16, "fp8": kpp.FP8_E4M3}
+    ebytes = {"f32": 4, "bf16": 2, "fp8": 1}
+
+    def store(dtype):
+        """The points as stored for `dtype`; quantisation (S0) timed apart."""
+        if dtype == "f32":
+            return x, None, 0.0
+        a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            a_.record(stream)
+            q = kpp.quantize(x, dtype)
+            b_.record(stream)
+        torch.cuda.synchronize(dev)
+        pts_, sc_ = (q, None) if dtype == "bf16" else q
+        return pts_, sc_, a_.elapsed_time(b_)
+
+    def time_form(dtype, pts, scales, steps, warmup):
+        """Tunes (untimed), then times `steps` seedings with CUDA events on the
+        launching stream, L2 flushed between them, clocks sampled."""
+        code = codes[dtype]
+        tuned = None
+        if not args.no_tune and not any(knobs):
+            t0 = time.time()
+            try:
+                best, tms = kpp.tune(pts, K, dtype=code, row_scales=scales,
+                                     passes=args.tune_passes)
+                tuned = {"options": {k: v for k, v in best.items() if v}, "ms_per_pass": tms,
+                         "seconds": round(time.time() - t0, 2)}
+            except kpp.KppError as e:
+                tuned = {"error": str(e)}
+        with torch.cuda.device(dev):
+            pst, plan = kpp.kpp_describe(N, d, K, code, opts)
+        if pst != kpp.OK:
+            raise kpp.KppError(pst, "kpp_describe")
+        plan = plan.as_dict()
+        ws = kpp.workspace_for(N, d, K, code, dev, opts)
+        idx = torch.empty(K, dtype=torch.int64, device=dev)
+        d2 = torch.empty(N, dtype=torch.float32, device=dev)
+        phi = torch.empty(1, dtype=torch.float64, device=dev)
+
+        def launch():
+            st = kpp.kpp_seed(pts.data_ptr(), None if scales is None else scales.data_ptr(), N,
+                              d, K, code, seed, stream_id, None, 0, idx.data_ptr(),
+                              d2.data_ptr(), phi.data_ptr(), ws.data_ptr(), ws.numel(), sh, opts)
+            if st != kpp.OK:
+                raise kpp.KppError(st, "kpp_seed")
+
+        with torch.cuda.stream(stream):
+            for _ in range(warmup):
+                flush.fill_(1)
+                launch()
+            st = kpp.kpp_read_status(ws.data_ptr(), sh)
+            if st != kpp.OK:
+                raise kpp.KppError(st, "warmup")
+            starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+            ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+            torch.cuda.synchronize(dev)
+            barrier()
+            torch.cuda.synchronize(dev)
+            sampler = ClockSampler(local)
+            sampler.start()
+            time.sleep(0.3)  # let the sampler take a first sample
+            for s_ in range(steps):
+                flush.fill_(s_ & 0xFF)  # L2 flush between steps, outside the events
+                starts[s_].record(stream)
+                launch()
+                ends[s_].record(stream)
+            torch.cuda.synchronize(dev)
+            clocks = sampler.stop()
+            barrier()
+            st = kpp.kpp_read_status(ws.data_ptr(), sh)
+            if st != kpp.OK:
+                raise kpp.KppError(st, "timed steps")
+        step_ms = [a_.elapsed_time(b_) for a_, b_ in zip(starts, ends)]
+        total_ms = multi.max_over_ranks(sum(step_ms), pg, dev)
+        # cheap invariants of the timed result (full parity lives in tests/)
+        idx_h = idx.cpu().numpy()
+        assert np.all((idx_h >= 0) & (idx_h < N)) and len(set(idx_h.tolist())) == K
+        assert float(d2[idx].abs().max()) == 0.0
+        form_name = {kpp.FORM_STREAMED: "streamed", kpp.FORM_PERSISTENT: "persistent",
+                     kpp.FORM_RECOMPUTE: "recompute"}[plan["form"]]
+        return {"idx": idx, "d2": d2, "phi": phi, "ws": ws, "plan": plan, "form": form_name,
+                "tuned": tuned, "ms": total_ms / steps, "step_ms": step_ms,
+                "clocks": clocks, "steps": steps}
+
+    def phi_gate(dtype, r):
+        """Cost distortion of a precision form's seeds: its own phi (its sum of
+        D^2 on its stored points) against the FP64-summed cost of the same
+        seeds on the original FP32 points (the FP32 path replayed on its
+        indices), and that cost against an FP32 seeding with the same draws."""
+        with torch.cuda.stream(stream):
+            phi_form = float(r["phi"].item())
+            _, _, phi_orig = kpp.seed(x, K, seed, stream_id, forced=r["idx"].clone(), check=True)
+            _, _, phi32 = kpp.seed(x, K, seed, stream_id, check=True)
+            torch.cuda.synchronize(dev)
+        phi_orig, phi32 = float(phi_orig.item()), float(phi32.item())
+        g = {"phi_form_own": phi_form, "phi_of_form_seeds_on_fp32_points": phi_orig,
+             "phi_rel_diff": abs(phi_form - phi_orig) / phi_orig,
+             "phi_gate_1e-3": abs(phi_form - phi_orig) <= 1e-3 * phi_orig,
+             "phi_fp32_same_seed": phi32, "phi_vs_fp32_run": (phi_orig - phi32) / phi32}
+        if args.phi_seeds > 1:
+            g["over_seeds"] = phi_over_seeds(kpp, x, r["pts"], r["scales"], codes[dtype], K,
+                                             wl.draw_seed, stream_id, args.phi_seeds, stream, dev)
+        return g
+
+    dtype = args.dtype
+    pts, scales, q_ms = store(dtype)
+    main_r = time_form(dtype, pts, scales, args.steps, args.warmup)
+    main_r["pts"], main_r["scales"] = pts, scales
+    ms_per_step = main_r["ms"]
+    nkd = float(N) * K * d
+    value = nkd * world / (ms_per_step / 1e3)
+    roofline = roofline_for(main_r["plan"], main_r["form"], N, d, K, ebytes[dtype],
+                            scales is not None, ms_per_step, wl.name, dtype, dev, peaks_live)
+    precision = None
+    if dtype != "f32" and not args.no_phi:
+        precision = phi_gate(dtype, main_r)
+        precision["quantize_ms"] = q_ms
+
+    # precision forms of the same data beside the FP32 headline
+    forms_block = None
+    forms = [] if (dtype != "f32" or args.forms in ("", "none")) else args.forms.split(",")
+    if forms:
+        forms_block = {}
+        for fd in forms:
+            fpts, fsc, fq_ms = store(fd)
+            fr = time_form(fd, fpts, fsc, max(1, min(args.steps, args.form_steps)),
+                           max(1, min(args.warmup, 2)))
+            fr["pts"], fr["scales"] = fpts, fsc
+            froof = roofline_for(fr["plan"], fr["form"], N, d, K, ebytes[fd], fsc is not None,
+                                 fr["ms"], wl.name, fd, dev, peaks_live)
+            entry = {"ms_per_seeding": fr["ms"], "value": nkd * world / (fr["ms"] / 1e3),
+                     "speedup_vs_f32": ms_per_step / fr["ms"], "steps": fr["steps"],
+                     "quantize_ms": fq_ms, "form": fr["form"], "plan": fr["plan"],
+                     "autotuner": fr["tuned"], "clocks": fr["clocks"],
+                     "gpu_launches": fr["plan"]["launches"] * fr["steps"],
+                     "roofline": {k: froof[k] for k in
+                                  ("bound", "achieved", "peak", "frac", "traffic",
+                                   "frac_of_hbm_read", "algorithmic_bytes_per_pass")
+                                  if k in froof}}
+            if not args.no_phi:
+                entry["phi"] = phi_gate(fd, fr)
+            forms_block[fd] = entry
+            del fpts, fsc, fr
+            torch.cuda.empty_cache()
+
+    # e2e: host points (pinned) -> C ABI -> host results, wall clock incl. copies
+    e2e = None
+    if not args.no_e2e:
+        xh = pts.cpu().pin_memory()
+        sh_host = None if scales is None else scales.cpu().pin_memory()
+        hidx, hd2, hphi, st, bufs = kpp.seed_host(xh, K, seed, stream_id, dtype=dtype,
+                                                  row_scales_host=sh_host, device=dev, opts=opts)
+        e2e_steps = max(1, min(args.steps, 5 if N * d * ebytes[dtype] < (1 << 30) else 3))
+        torch.cuda.synchronize(dev)
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            hidx, hd2, hphi, st, bufs = kpp.seed_host(xh, K, seed, stream_id, dtype=dtype,
+                                                      row_scales_host=sh_host, device=dev,
+                                                      opts=opts, buffers=bufs)
+            if st != kpp.OK:
+                raise kpp.KppError(st, "kpp_seed_host")
+        e2e_s = multi.max_over_ranks(time.perf_counter() - t0, pg, dev)
+        h2d = N * d * ebytes[dtype] + (4 * N if scales is not None else 0)
+        d2h = 8 * K + 4 * N + 8
+        e2e = {"value": nkd * world * e2e_steps / e2e_s, "unit": UNIT,
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "ms_per_step": 1e3 * e2e_s / e2e_steps, "steps": e2e_steps}
+        del xh, sh_host, bufs
+
+    cpu_baseline = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        stored = x_np if dtype == "f32" else (
+            pts.cpu().numpy().view(np.uint16) if dtype == "bf16" else pts.cpu().numpy())
+        if stored is None:
+            stored = x.cpu().numpy()
+        sc_np = None if scales is None else scales.cpu().numpy()
+        cpu_baseline = oracle_baseline(stored, sc_np, K, seed, stream_id)
+
+    if rank == 0:
+        plan = main_r["plan"]
+        print(json.dumps({
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": dtype, "data": "synthetic",
+            "config": {"workload": wl.name, "N": N, "d": d, "K": K, "storage": dtype,
+                       "form": main_r["form"], "plan": plan, "autotuner": main_r["tuned"],
+                       "parallelism": f"replicas{world}",
+                       "l2": "flushed between steps (512 MiB write)",
+                       "step_ms_min": min(main_r["step_ms"]),
+                       "step_ms_max": max(main_r["step_ms"])},
+            "clocks": main_r["clocks"], "e2e": e2e,
+            "gpu_launches": plan["launches"] * args.steps,
+            "precision": precision, "forms": forms_block,
+            "read_peaks": peaks_live,
+            "roofline": roofline, "cpu_baseline": cpu_baseline,
+        }), flush=True)
+
+
+def oracle_baseline(stored, scales, K, seed, stream_id, budget_s: float = 15.0):
+    """The multi-threaded FP64 oracle on all host cores, on the workload's
+    stored points, for as many of the K passes as fit about `budget_s`
+    seconds (calibrated on a 2-pass run); N*K*d per second."""
+    import oracle
+
+    N, d = stored.shape
+    cores, model = cpu_info()
+    t0 = time.perf_counter()
+    r = oracle.seed_mt(stored, min(2, K), seed, stream_id, scales=scales, threads=cores)
+    per_pass = (time.perf_counter() - t0) / min(2, K)
+    K_s = int(max(1, min(K, budget_s / max(per_pass, 1e-9))))
+    t0 = time.perf_counter()
+    r = oracle.seed_mt(stored, K_s, seed, stream_id, scales=scales, threads=cores)
+    dt = time.perf_counter() - t0
+    return {"value": N * K_s * d / dt, "unit": UNIT, "cores": r["threads"], "kind": "oracle",
+            "sample": f"full workload data ({N} x {d}), first {K_s} of {K} passes, "
+                      f"multi-threaded FP64 oracle on {r['threads']} threads ({dt:.1f} s)",
+            "host_cores": cores, "cpu": model, "seconds": dt}
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -792,197 +1132,7 @@ def main():
     if args.workload.startswith(KMPAR_PREFIX):
         run_kmpar(args, rank, world, dev, pg, barrier)
         return
-    wl = datagen.WORKLOADS[args.workload]
-    if args.n_points or args.k_seeds:
-        import dataclasses
-
-        n_, k_ = args.n_points or wl.N, args.k_seeds or wl.K
-        wl = dataclasses.replace(wl, N=n_, K=k_, name=f"{wl.name}@N{n_}K{k_}")
-    x_np = datagen.workload_points(wl) if wl.N <= 2_000_000 else None
-    x = torch.from_numpy(x_np).to(dev) if x_np is not None else datagen.workload_points(wl, dev)
-    N, d, K = wl.N, wl.d, wl.K
-    scales = None
-    if args.dtype == "f32":
-        pts = x
-    elif args.dtype == "bf16":
-        pts = kpp.quantize(x, "bf16")
-    else:
-        pts, scales = kpp.quantize(x, "fp8")
-    eb = {"f32": 4, "bf16": 2, "fp8": 1}[args.dtype]
-    opts = kpp.Options()
-    opts.form = args.form
-    opts.lanes_per_row = args.lanes
-    opts.ctas_per_sm = args.ctas_per_sm
-    opts.smem_cache = args.smem_cache
-    opts.alternate = args.alternate
-    opts.l2_policy = args.l2_policy
-    opts.min_rows_per_cta = args.min_rows
-    code = {"f32": kpp.F32, "bf16": kpp.BF16, "fp8": kpp.FP8_E4M3}[args.dtype]
-    # the autotuner picks form, lanes per row, row block and cache (untimed);
-    # kpp_seed's automatic choice then uses its winner for this shape
-    knobs = (args.form, args.lanes, args.ctas_per_sm, args.smem_cache, args.alternate,
-             args.l2_policy, args.min_rows)
-    tuned = None
-    if not args.no_tune and not any(knobs):
-        t0 = time.time()
-        try:
-            best, tms = kpp.tune(pts, K, dtype=code, row_scales=scales, passes=args.tune_passes)
-            tuned = {"options": {k: v for k, v in best.items() if v}, "ms_per_pass": tms,
-                     "seconds": round(time.time() - t0, 2)}
-        except kpp.KppError as e:
-            tuned = {"error": str(e)}
-    with torch.cuda.device(dev):
-        pst, plan = kpp.kpp_describe(N, d, K, code, opts)
-    if pst != kpp.OK:
-        raise kpp.KppError(pst, "kpp_describe")
-    plan = plan.as_dict()
-    form_name = {kpp.FORM_STREAMED: "streamed", kpp.FORM_PERSISTENT: "persistent",
-                 kpp.FORM_RECOMPUTE: "recompute"}[plan["form"]]
-    ws = kpp.workspace_for(N, d, K, code, dev, opts)
-    idx = torch.empty(K, dtype=torch.int64, device=dev)
-    d2 = torch.empty(N, dtype=torch.float32, device=dev)
-    phi = torch.empty(1, dtype=torch.float64, device=dev)
-    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
-    stream = torch.cuda.Stream(dev)
-    sh = __import__("ctypes").c_void_p(stream.cuda_stream)
-    seed = wl.draw_seed
-    stream_id = multi.replica_stream(0, rank)
-
-    def launch():
-        st = kpp.kpp_seed(pts.data_ptr(), None if scales is None else scales.data_ptr(), N, d, K,
-                          code, seed, stream_id, None, 0, idx.data_ptr(), d2.data_ptr(),
-                          phi.data_ptr(), ws.data_ptr(), ws.numel(), sh, opts)
-        if st != kpp.OK:
-            raise kpp.KppError(st, "kpp_seed")
-
-    with torch.cuda.stream(stream):
-        for _ in range(args.warmup):
-            flush.fill_(1)
-            launch()
-        st = kpp.kpp_read_status(ws.data_ptr(), sh)
-        if st != kpp.OK:
-            raise kpp.KppError(st, "warmup")
-        starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-        ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-        torch.cuda.synchronize(dev)
-        barrier()
-        torch.cuda.synchronize(dev)
-        sampler = ClockSampler(local)
-        sampler.start()
-        time.sleep(0.3)  # let the sampler take a first sample
-        for s in range(args.steps):
-            flush.fill_(s & 0xFF)  # L2 flush between steps, outside the events
-            starts[s].record(stream)
-            launch()
-            ends[s].record(stream)
-        torch.cuda.synchronize(dev)
-        clocks = sampler.stop()
-        barrier()
-    step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
-    total_ms = multi.max_over_ranks(sum(step_ms), pg, dev)
-    ms_per_step = total_ms / args.steps
-    nkd = float(N) * K * d
-    value = nkd * world * args.steps / (total_ms / 1e3)
-    # parity of the timed result (cheap invariants; full parity lives in tests/)
-    idx_h = idx.cpu().numpy()
-    assert np.all((idx_h >= 0) & (idx_h < N)) and len(set(idx_h.tolist())) == K
-    assert float(d2[idx].abs().max()) == 0.0
-
-    # precision forms: cost of this form's seeds on the original FP32 points,
-    # evaluated by replaying its indices through the FP32 path
-    precision = None
-    if args.dtype != "f32" and not args.no_phi:
-        with torch.cuda.stream(stream):
-            phi_form = float(phi.item())
-            _, _, phi_orig = kpp.seed(x, K, seed, stream_id, forced=idx.clone(), check=True)
-            i32, _, phi32 = kpp.seed(x, K, seed, stream_id, check=True)
-            torch.cuda.synchronize(dev)
-        phi_orig = float(phi_orig.item())
-        phi32 = float(phi32.item())
-        precision = {"phi_form_own": phi_form, "phi_of_form_seeds_on_fp32_points": phi_orig,
-                     "phi_rel_diff": abs(phi_form - phi_orig) / phi_orig,
-                     "phi_fp32_same_seed": phi32,
-                     "phi_vs_fp32_run": (phi_orig - phi32) / phi32}
-        if args.phi_seeds > 1:
-            precision["over_seeds"] = phi_over_seeds(kpp, x, pts, scales, code, K, wl.draw_seed,
-                                                     stream_id, args.phi_seeds, stream, dev)
-
-    # e2e: host points (pinned) -> C ABI -> host results, wall clock incl. copies
-    e2e = None
-    if not args.no_e2e:
-        xh = pts.cpu().pin_memory()
-        sh_host = None if scales is None else scales.cpu().pin_memory()
-        bufs = None
-        hidx, hd2, hphi, st, bufs = kpp.seed_host(xh, K, seed, stream_id, dtype=args.dtype,
-                                                  row_scales_host=sh_host, device=dev, opts=opts)
-        e2e_steps = max(1, min(args.steps, 5))
-        torch.cuda.synchronize(dev)
-        barrier()
-        t0 = time.perf_counter()
-        for _ in range(e2e_steps):
-            hidx, hd2, hphi, st, bufs = kpp.seed_host(xh, K, seed, stream_id, dtype=args.dtype,
-                                                      row_scales_host=sh_host, device=dev,
-                                                      opts=opts, buffers=bufs)
-            if st != kpp.OK:
-                raise kpp.KppError(st, "kpp_seed_host")
-        e2e_s = multi.max_over_ranks(time.perf_counter() - t0, pg, dev)
-        h2d = N * d * eb + (4 * N if scales is not None else 0)
-        d2h = 8 * K + 4 * N + 8
-        e2e = {"value": nkd * world * e2e_steps / e2e_s, "unit": UNIT,
-               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-               "ms_per_step": 1e3 * e2e_s / e2e_steps}
-
-    # roofline of the dominant kernel: the persistent kernel (one launch per
-    # seeding) or the per-pass streamed kernel (K launches per seeding)
-    peaks = measured_peaks()
-    peak = peaks["hbm_gbs"] if peaks else 6800.0
-    launches_per_step = plan["launches"]
-    per_launch_ms = ms_per_step / launches_per_step
-    passes_per_launch = K // launches_per_step
-    point_bytes = N * d * eb + (4 * N if scales is not None else 0)
-    d2_bytes = 8 * N if form_name == "streamed" else 0  # D^2 stays on chip when persistent
-    alg_bytes = passes_per_launch * (point_bytes + d2_bytes)
-    achieved = alg_bytes / (per_launch_ms / 1e3) / 1e9
-    traffic = (profiled_traffic(form_name, wl.name, args.dtype, plan)
-               if form_name in KERNEL_SOURCES else None)
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": traffic,
-                "peak_source": "measured" if peaks else "fallback",
-                "kernel": f"{form_name}_kernel", "algorithmic_bytes_per_launch": alg_bytes,
-                "algorithmic_bytes_per_pass": point_bytes + d2_bytes}
-
-    cpu_baseline = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        import oracle
-
-        stored = x_np if args.dtype == "f32" else (
-            pts.cpu().numpy().view(np.uint16) if args.dtype == "bf16" else pts.cpu().numpy())
-        if stored is None:
-            stored = x.cpu().numpy()
-        K_s = oracle_sample_passes(wl)
-        sc_np = None if scales is None else scales.cpu().numpy()
-        dt_s = time_oracle(stored, wl, K_s, seed, stream_id, sc_np)
-        cores, model = cpu_info()
-        cpu_baseline = {"value": N * K_s * d / dt_s, "unit": UNIT, "cores": 1, "kind": "oracle",
-                        "sample": f"full workload data, first {K_s} of {K} passes "
-                                  f"(serial FP64 oracle, {dt_s:.1f} s)",
-                        "host_cores": cores, "cpu": model}
-
-    if rank == 0:
-        print(json.dumps({
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": args.dtype, "data": "synthetic",
-            "config": {"workload": wl.name, "N": N, "d": d, "K": K, "storage": args.dtype,
-                       "form": form_name, "plan": plan, "autotuner": tuned,
-                       "parallelism": f"replicas{world}",
-                       "l2": "flushed between steps (512 MiB write)",
-                       "step_ms_min": min(step_ms), "step_ms_max": max(step_ms)},
-            "clocks": clocks, "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
-            "precision": precision,
-            "roofline": roofline, "cpu_baseline": cpu_baseline,
-        }), flush=True)
+    run_seeding(args, rank, world, local, dev, pg, barrier)
     if pg is not None:
         pg.destroy_process_group()
 

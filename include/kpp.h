@@ -106,7 +106,14 @@ typedef struct {
     int32_t l2_policy;        /* persistent form, streamed rows: 0 = evict-last,
                                  -1 = no hint, 2 = evict-first */
     int32_t min_rows_per_cta; /* persistent form: smallest row block; 0 = 2048 */
-    int32_t reserved[3];
+    int32_t exact_draws;      /* 1 = decide every "prefix > t" comparison of every draw
+                                 in FP64 (t = u * T as the FP64 product of the draw's
+                                 uniform and the pair total), the path otherwise taken
+                                 only at near ties, where an FP32 estimate of the
+                                 prefix lies within 2^-40 t of t; same results, slower
+                                 draws; for testing that path.  0 = FP32 estimates
+                                 decide away from ties (default) */
+    int32_t reserved[2];
 } kpp_options;
 
 /* The launch plan kpp_seed would use for a problem (filled by kpp_describe). */
@@ -209,6 +216,23 @@ KPP_API kpp_status kpp_read_status(const void *workspace, kpp_stream_t stream);
  */
 KPP_API kpp_status kpp_quantize(const float *x, int64_t N, int32_t d, kpp_dtype to, void *out,
                         float *row_scales, kpp_stream_t stream);
+
+/*
+ * Measurement utility (not part of the method; the paper has no
+ * counterpart): the rate at which this GPU streams reads from a buffer, the
+ * denominator a seeding pass -- a pure read stream over the points -- is
+ * compared with.  Reads `bytes` of `buf` once untimed, then `reps` times,
+ * with one full wave of resident CTAs issuing 16-byte loads, timed with CUDA
+ * events on `stream`; *ms_out (host) receives the mean milliseconds per
+ * timed sweep.  A buffer far larger than L2 gives the HBM read bandwidth; a
+ * buffer well inside L2, read again and again, the L2 read bandwidth.
+ *   buf    device, 16-byte aligned; bytes a multiple of 16 (>= 16)
+ *   reps   >= 1
+ * Blocks the calling thread (it waits for the last sweep).  Returns KPP_OK,
+ * KPP_ERR_INVALID_ARG, KPP_ERR_LAUNCH or KPP_ERR_CUDA.
+ */
+KPP_API kpp_status kpp_measure_read(const void *buf, size_t bytes, int32_t reps,
+                                    kpp_stream_t stream, float *ms_out);
 
 /*
  * Batching form (not in the paper): many independent seedings -- of uneven
@@ -401,6 +425,11 @@ KPP_API kpp_status kpp_kmeans_par(const float *points, int64_t N, int32_t d, int
  *
  * The first call on each device looks up the array's device address while
  * that device is current; make that first call before any stream capture.
+ * The address is kept with the device's context: after the context is
+ * replaced (cudaDeviceReset), the next call looks it up again, and that
+ * call too belongs before any capture.  Plans have one CTA per SM (at most
+ * 152 on a GB300) unless opts asks for more per SM and they fit; a plan of
+ * more than 252 CTAs is rejected as said above.
  * All calls share the one array and it keeps the last call's contents (each
  * call clears what must start at zero), so calls whose work overlaps on the
  * GPU -- on different streams, or from different threads -- race; serialise

@@ -63,7 +63,7 @@ def build(force: bool = False) -> str:
     if force or stale:
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
         cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-std=c11",
-               "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"]
+               "-shared", "-fPIC", "-pthread", "-o", tmp, _SRC, "-lm"]
         subprocess.run(cmd, check=True)
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -96,6 +96,10 @@ def _load():
             P, P, ctypes.c_int, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
             ctypes.c_uint64, ctypes.c_uint64, P, ctypes.c_int32, P, P, P, P, P]
         lib.kpp_oracle_seed.restype = ctypes.c_int
+        lib.kpp_oracle_seed_mt.argtypes = [
+            P, P, ctypes.c_int, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+            ctypes.c_uint64, ctypes.c_uint64, P, P, P, ctypes.c_int32]
+        lib.kpp_oracle_seed_mt.restype = ctypes.c_int
         lib.kpp_oracle_lloyd_step.argtypes = [
             P, P, ctypes.c_int, ctypes.c_int64, ctypes.c_int32, P, ctypes.c_int32, P, P, P, P, P]
         lib.kpp_oracle_lloyd_step.restype = ctypes.c_int
@@ -230,6 +234,30 @@ def seed(points: np.ndarray, K: int, seed: int, stream: int = 0, *, dtype=None,
     if history:
         out["d2_hist"] = hist
     return out
+
+
+def seed_mt(points: np.ndarray, K: int, seed: int, stream: int = 0, *, dtype=None,
+            scales: np.ndarray | None = None, threads: int | None = None) -> dict:
+    """Multi-threaded FP64 seeding (the CPU baseline on all host cores).
+
+    Algorithm 1 with readings R1-R6, the points split into ``threads``
+    contiguous chunks: D^2 bit-identical to ``seed``; the draw's prefix sums
+    regrouped at chunk boundaries (identical to ``seed`` on integer data).
+    Returns a dict with ``idx``, ``d2``, ``phi``, ``status`` and ``threads``.
+    """
+    pts = np.ascontiguousarray(points)
+    N, d = pts.shape
+    code = _dtype_code(pts, dtype)
+    sc = None if scales is None else np.ascontiguousarray(scales, dtype=np.float32)
+    nt = int(threads or os.cpu_count() or 1)
+    idx = np.empty(K, dtype=np.int64)
+    d2 = np.empty(N, dtype=np.float64)
+    phi = np.zeros(1, dtype=np.float64)
+    st = _load().kpp_oracle_seed_mt(_ptr(pts), _ptr(sc), code, N, d, K, seed, stream, _ptr(idx),
+                                    _ptr(d2), _ptr(phi), nt)
+    if st == INVALID:
+        raise ValueError("oracle rejected its arguments")
+    return {"idx": idx, "d2": d2, "phi": float(phi[0]), "status": st, "threads": min(nt, N)}
 
 
 def lloyd_step(points: np.ndarray, centres: np.ndarray, *, dtype=None,

@@ -81,7 +81,9 @@
  * Build: gcc -O2 -ffp-contract=off -shared -fPIC (no fused multiply-add, so
  * the arithmetic is the one written here on every host).
  */
+#define _POSIX_C_SOURCE 200809L /* pthread barriers under -std=c11 */
 #include <math.h>
+#include <pthread.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -680,5 +682,208 @@ int kpp_oracle_kmeans_par(const void *points, const float *scales, int dtype, in
     free(pos);
     free(D2);
     free(flags);
+    return status;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Multi-threaded seeding (Algorithm 1, readings R1-R6), for the CPU baseline */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * The same seeding as kpp_oracle_seed, run by n_threads POSIX threads so that
+ * a timing of the oracle uses every host core.  The points are split into
+ * n_threads contiguous chunks [t*N/n, (t+1)*N/n).  In every pass each thread
+ * takes the FP64 difference-form distance of each point of its chunk to the
+ * newest seed (R5, the same operations as the serial oracle, so D^2 is
+ * bit-identical to it), keeps the minimum, and sums its chunk's D^2
+ * sequentially in FP64.  The draw (R3) then adds the chunk sums in chunk
+ * order to form T and t = u_m * T, walks them in order to the first chunk
+ * whose running total exceeds t, and rescans that chunk sequentially from
+ * the total before it for the first point whose prefix exceeds t -- the
+ * prefix P_i of R3 with the sequential sum regrouped at chunk boundaries
+ * (identical on integer data, where every sum is exact).  If rounding leaves
+ * the rescan short of t, the chunk's last point with D^2 > 0 is taken; if no
+ * chunk total exceeds t, the last point with D^2 > 0 overall.  Coordinates are
+ * decoded on the fly (no N x d FP64 copy of the points).
+ *   idx_out [K], d2_out [N], phi_out [1] or NULL; n_threads >= 1.
+ * Returns KPP_ORACLE_OK, KPP_ORACLE_INVALID or KPP_ORACLE_DEGENERATE (R4).
+ */
+typedef struct {
+    const void *points;
+    const float *scales;
+    int dtype;
+    int64_t N;
+    int32_t d;
+    int32_t n_threads; /* threads actually running (chunks) */
+    double *d2;
+    double *centre;    /* [d] decoded coordinates of the newest seed */
+    double *chunk_sum; /* [n_threads] */
+    int first_pass;
+    int stop;
+    int ready; /* barriers initialised for n_threads: workers may start */
+    pthread_mutex_t mu;
+    pthread_cond_t cv;
+    pthread_barrier_t start, done;
+} mt_shared;
+
+typedef struct {
+    mt_shared *sh;
+    int32_t tid;
+} mt_arg;
+
+static int64_t mt_chunk_begin(const mt_shared *sh, int32_t t)
+{
+    return sh->N * (int64_t)t / sh->n_threads;
+}
+
+static void mt_pass(mt_shared *sh, int32_t t)
+{
+    const int64_t b = mt_chunk_begin(sh, t), e = mt_chunk_begin(sh, t + 1);
+    double s = 0.0;
+    for (int64_t i = b; i < e; ++i) {
+        double delta = 0.0;
+        for (int32_t j = 0; j < sh->d; ++j) {
+            double diff = coord(sh->points, sh->scales, sh->dtype, i, sh->d, j) - sh->centre[j];
+            delta += diff * diff;
+        }
+        if (sh->first_pass || delta < sh->d2[i])
+            sh->d2[i] = delta;
+        s += sh->d2[i];
+    }
+    sh->chunk_sum[t] = s;
+}
+
+static void *mt_worker(void *p)
+{
+    mt_arg *a = (mt_arg *)p;
+    mt_shared *sh = a->sh;
+    pthread_mutex_lock(&sh->mu);
+    while (!sh->ready)
+        pthread_cond_wait(&sh->cv, &sh->mu);
+    pthread_mutex_unlock(&sh->mu);
+    for (;;) {
+        pthread_barrier_wait(&sh->start);
+        if (sh->stop)
+            break;
+        mt_pass(sh, a->tid);
+        pthread_barrier_wait(&sh->done);
+    }
+    return NULL;
+}
+
+int kpp_oracle_seed_mt(const void *points, const float *scales, int dtype, int64_t N,
+                       int32_t d, int32_t K, uint64_t seed, uint64_t stream, int64_t *idx_out,
+                       double *d2_out, double *phi_out, int32_t n_threads)
+{
+    if (!points || !idx_out || !d2_out || N < 1 || d < 1 || K < 1 || K > N || n_threads < 1 ||
+        dtype < 0 || dtype > 2 || (dtype == KPP_ORACLE_FP8_E4M3 && !scales))
+        return KPP_ORACLE_INVALID;
+    if ((int64_t)n_threads > N)
+        n_threads = (int32_t)N;
+    mt_shared sh;
+    memset(&sh, 0, sizeof(sh));
+    sh.points = points;
+    sh.scales = scales;
+    sh.dtype = dtype;
+    sh.N = N;
+    sh.d = d;
+    sh.d2 = d2_out;
+    sh.centre = (double *)malloc(sizeof(double) * (size_t)d);
+    sh.chunk_sum = (double *)malloc(sizeof(double) * (size_t)n_threads);
+    pthread_t *th = (pthread_t *)malloc(sizeof(pthread_t) * (size_t)n_threads);
+    mt_arg *args = (mt_arg *)malloc(sizeof(mt_arg) * (size_t)n_threads);
+    if (!sh.centre || !sh.chunk_sum || !th || !args) {
+        free(sh.centre);
+        free(sh.chunk_sum);
+        free(th);
+        free(args);
+        return KPP_ORACLE_INVALID;
+    }
+    pthread_mutex_init(&sh.mu, NULL);
+    pthread_cond_init(&sh.cv, NULL);
+    /* workers wait until the barriers exist; if a thread cannot be created,
+       the chunks are split over the threads that were */
+    int32_t started = 1;
+    for (int32_t t = 1; t < n_threads; ++t) {
+        args[t].sh = &sh;
+        args[t].tid = t;
+        if (pthread_create(&th[t], NULL, mt_worker, &args[t]) != 0)
+            break;
+        ++started;
+    }
+    sh.n_threads = started;
+    pthread_barrier_init(&sh.start, NULL, (unsigned)started);
+    pthread_barrier_init(&sh.done, NULL, (unsigned)started);
+    pthread_mutex_lock(&sh.mu);
+    sh.ready = 1;
+    pthread_cond_broadcast(&sh.cv);
+    pthread_mutex_unlock(&sh.mu);
+
+    int status = KPP_ORACLE_OK;
+    for (int32_t m = 0; m < K; ++m)
+        idx_out[m] = -1;
+    double u0 = kpp_oracle_uniform(seed, stream, 0); /* R2 */
+    int64_t first = (int64_t)floor(u0 * (double)N);
+    idx_out[0] = first > N - 1 ? N - 1 : first;
+    for (int32_t m = 0; m < K; ++m) {
+        for (int32_t j = 0; j < d; ++j)
+            sh.centre[j] = coord(points, scales, dtype, idx_out[m], d, j);
+        sh.first_pass = (m == 0);
+        pthread_barrier_wait(&sh.start);
+        mt_pass(&sh, 0);
+        pthread_barrier_wait(&sh.done);
+        if (m == K - 1)
+            break;
+        double T = 0.0;
+        for (int32_t t = 0; t < sh.n_threads; ++t)
+            T += sh.chunk_sum[t];
+        if (T == 0.0) { /* R4 */
+            status = KPP_ORACLE_DEGENERATE;
+            break;
+        }
+        const double tt = kpp_oracle_uniform(seed, stream, (uint64_t)(m + 1)) * T;
+        int64_t pick = -1;
+        double run = 0.0;
+        for (int32_t c = 0; c < sh.n_threads; ++c) {
+            if (run + sh.chunk_sum[c] > tt) {
+                const int64_t b = mt_chunk_begin(&sh, c), e = mt_chunk_begin(&sh, c + 1);
+                double P = run;
+                int64_t lastpos = -1;
+                for (int64_t i = b; i < e && pick < 0; ++i) {
+                    if (d2_out[i] > 0.0)
+                        lastpos = i;
+                    P += d2_out[i];
+                    if (P > tt)
+                        pick = i;
+                }
+                if (pick < 0)
+                    pick = lastpos;
+                break;
+            }
+            run += sh.chunk_sum[c];
+        }
+        for (int64_t i = N - 1; pick < 0 && i >= 0; --i)
+            if (d2_out[i] > 0.0)
+                pick = i;
+        idx_out[m + 1] = pick;
+    }
+    sh.stop = 1;
+    pthread_barrier_wait(&sh.start);
+    for (int32_t t = 1; t < started; ++t)
+        pthread_join(th[t], NULL);
+    if (status == KPP_ORACLE_OK && phi_out) {
+        double phi = 0.0;
+        for (int32_t t = 0; t < sh.n_threads; ++t)
+            phi += sh.chunk_sum[t];
+        *phi_out = phi;
+    }
+    pthread_barrier_destroy(&sh.start);
+    pthread_barrier_destroy(&sh.done);
+    pthread_cond_destroy(&sh.cv);
+    pthread_mutex_destroy(&sh.mu);
+    free(sh.centre);
+    free(sh.chunk_sum);
+    free(th);
+    free(args);
     return status;
 }

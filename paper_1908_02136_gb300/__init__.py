@@ -47,7 +47,8 @@ class Options(ctypes.Structure):
                 ("ctas_per_sm", ctypes.c_int32), ("use_graph", ctypes.c_int32),
                 ("timeout_us", ctypes.c_uint32), ("smem_cache", ctypes.c_int32),
                 ("alternate", ctypes.c_int32), ("l2_policy", ctypes.c_int32),
-                ("min_rows_per_cta", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("min_rows_per_cta", ctypes.c_int32), ("exact_draws", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
 
 
 class Plan(ctypes.Structure):
@@ -117,6 +118,8 @@ def load_library(build_if_stale: bool = True):
         lib.kpp_read_status.restype = ctypes.c_int
         lib.kpp_quantize.argtypes = [P, I64, I32, ctypes.c_int, P, P, P]
         lib.kpp_quantize.restype = ctypes.c_int
+        lib.kpp_measure_read.argtypes = [P, ctypes.c_size_t, I32, P, P]
+        lib.kpp_measure_read.restype = ctypes.c_int
         lib.kpp_tune_workspace_size.argtypes = [I64, I32, I32, ctypes.c_int]
         lib.kpp_tune_workspace_size.restype = ctypes.c_size_t
         lib.kpp_tune.argtypes = [P, P, I64, I32, I32, ctypes.c_int, P, P, P, ctypes.c_size_t, P,
@@ -219,6 +222,25 @@ def kpp_read_status(workspace, stream) -> int:
 
 def kpp_quantize(x, N, d, to, out, row_scales, stream) -> int:
     return load_library().kpp_quantize(x, N, d, to, out, row_scales, stream)
+
+
+def kpp_measure_read(buf, nbytes, reps, stream, ms_out) -> int:
+    return load_library().kpp_measure_read(buf, nbytes, reps, stream, ms_out)
+
+
+def measure_read_gbs(nbytes: int, reps: int, device="cuda") -> float:
+    """Read bandwidth (GB/s) of this GPU over a buffer of ``nbytes`` bytes,
+    read ``reps`` times after one untimed sweep (``kpp_measure_read``)."""
+    import torch
+
+    dev = torch.device(device)
+    buf = torch.ones(nbytes // 4, dtype=torch.int32, device=dev)
+    ms = ctypes.c_float(0.0)
+    st = kpp_measure_read(buf.data_ptr(), buf.numel() * 4, reps, _stream_handle(dev),
+                          ctypes.byref(ms))
+    if st != OK:
+        raise KppError(st, "kpp_measure_read")
+    return buf.numel() * 4 / (ms.value * 1e-3) / 1e9
 
 
 def kpp_tune_workspace_size(N, d, K, dtype) -> int:
@@ -370,7 +392,7 @@ def tune(points, K: int, *, dtype=None, row_scales=None, passes: int = 0):
                       _stream_handle(dev), passes, best, ms)
     if st != OK:
         raise KppError(st, "kpp_tune")
-    return {f: getattr(best, f) for f, _ in Options._fields_ if f != "reserved"}, ms.value
+    return {f: getattr(best, f) for f, _ in Options._fields_ if f not in ("reserved", "exact_draws")}, ms.value
 
 
 class Lloyd:

@@ -458,6 +458,7 @@ kpp_status kpp_seed(const void *points, const float *row_scales, int64_t N, int3
     }
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     p.recompute = pl.form == KPP_FORM_RECOMPUTE ? 1 : 0;
+    p.exact_draws = (opts && opts->exact_draws) ? 1 : 0;
     if (pl.form == KPP_FORM_PERSISTENT)
         return run_persistent(pl, p, s);
     const int use_graph = opts ? opts->use_graph : 0;

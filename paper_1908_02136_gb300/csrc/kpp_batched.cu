@@ -290,6 +290,7 @@ kpp_status kpp_seed_batched(const kpp_problem *problems, int32_t n, kpp_dtype dt
         p.chunk = bp.chunk[i];
         p.nblocks = bp.nblocks[i];
         p.slots = reinterpret_cast<unsigned long long *>(ws + bp.off_slots + bp.slot_off[i]);
+        p.exact_draws = (opts && opts->exact_draws) ? 1 : 0;
         b.d = q.d;
     }
     if (cudaMemsetAsync(ws, 0, bp.bytes, s) != cudaSuccess ||

@@ -55,7 +55,7 @@ struct Problem {
     unsigned long long *slots; // persistent form: [2][nblocks * kSlotWords] tagged block sums
     unsigned long long *mail;  // persistent form: the drawn index, tagged with its pass
     int32_t recompute;         // streamed form: every pass rebuilds D^2 from all chosen seeds
-    int32_t pad_;
+    int32_t exact_draws;       // every draw decision in FP64 (the near-tie path), for testing
 };
 
 // ---------------------------------------------------------------------------
@@ -307,7 +307,8 @@ struct Thresh {
     float uh, ul; // u split into two floats
     double u;
     Pair T;
-    int inf; // t = +infinity: no prefix exceeds it
+    int inf;   // t = +infinity: no prefix exceeds it
+    int all_exact; // every decision in FP64 (tol = +infinity)
 
     __device__ __forceinline__ double exact() const
     {
@@ -328,9 +329,12 @@ struct Thresh {
 };
 
 // u and its float split; the FP64 work here is off the draw's critical path.
-__device__ __forceinline__ Thresh thresh_for_u(double u)
+// `exact`: no decision is left to the FP32 estimate (the near-tie path is
+// taken at every comparison).
+__device__ __forceinline__ Thresh thresh_for_u(double u, int exact = 0)
 {
     Thresh th;
+    th.all_exact = exact;
     th.u = u;
     th.uh = (float)u;
     th.ul = (float)(u - (double)th.uh);
@@ -349,7 +353,7 @@ __device__ __forceinline__ void thresh_set_total(Thresh &th, const Pair &T)
     const float e = __fmaf_rn(th.uh, T.hi, -p);
     th.hi = p;
     th.lo = __fadd_rn(e, __fmaf_rn(th.uh, T.lo, __fmul_rn(th.ul, T.hi)));
-    th.tol = fabsf(p) * 0x1.0p-40f + 0x1.0p-126f;
+    th.tol = th.all_exact ? __int_as_float(0x7f800000) : fabsf(p) * 0x1.0p-40f + 0x1.0p-126f;
 }
 
 __device__ __forceinline__ Thresh thresh_inf()

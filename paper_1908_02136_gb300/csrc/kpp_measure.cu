@@ -1,0 +1,89 @@
+// kpp_measure.cu -- kpp_measure_read: the rate at which this GPU streams
+// reads from a buffer, the denominator the seeding passes are compared with.
+// A seeding pass only reads its points (no write stream), so a copy-based
+// bandwidth figure (read + write) understates what a pure read stream can
+// reach; this kernel measures the pure read rate, from HBM (a buffer much
+// larger than L2) or from L2 (a small buffer read again and again).
+#include "kpp.h"
+#include "kpp_internal.h"
+
+namespace kpp {
+namespace {
+
+constexpr int kReadThreads = 512;
+constexpr int kReadUnroll = 8;
+
+// Sink of the XOR of everything read, stored only when it takes one
+// particular value: the loads cannot be dropped, and the store (almost)
+// never happens.
+__device__ uint32_t g_read_sink;
+
+__global__ void __launch_bounds__(kReadThreads) read_kernel(const uint4 *buf, int64_t n)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t acc = 0;
+    // kReadUnroll independent 16-byte loads in flight per thread
+    for (; i + (kReadUnroll - 1) * stride < n; i += kReadUnroll * stride) {
+        uint4 v[kReadUnroll];
+#pragma unroll
+        for (int u = 0; u < kReadUnroll; ++u)
+            v[u] = ld_stream16(buf + i + u * stride);
+#pragma unroll
+        for (int u = 0; u < kReadUnroll; ++u)
+            acc ^= v[u].x ^ v[u].y ^ v[u].z ^ v[u].w;
+    }
+    for (; i < n; i += stride) {
+        const uint4 v = ld_stream16(buf + i);
+        acc ^= v.x ^ v.y ^ v.z ^ v.w;
+    }
+    if (acc == 0x9e3779b9u)
+        g_read_sink = acc;
+}
+
+} // namespace
+} // namespace kpp
+
+using namespace kpp;
+
+extern "C" kpp_status kpp_measure_read(const void *buf, size_t bytes, int32_t reps,
+                                       kpp_stream_t stream, float *ms_out)
+{
+    if (!buf || !ms_out || reps < 1 || bytes < 16 || (bytes % 16) != 0 ||
+        (reinterpret_cast<uintptr_t>(buf) % 16) != 0)
+        return KPP_ERR_INVALID_ARG;
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, read_kernel, kReadThreads, 0) !=
+            cudaSuccess)
+        return KPP_ERR_CUDA;
+    if (per_sm < 1)
+        per_sm = 1;
+    const int grid = sms * per_sm; // one full wave of resident CTAs
+    const int64_t n = (int64_t)(bytes / 16);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
+        if (a)
+            cudaEventDestroy(a);
+        return KPP_ERR_CUDA;
+    }
+    kpp_status st = KPP_OK;
+    read_kernel<<<grid, kReadThreads, 0, s>>>(reinterpret_cast<const uint4 *>(buf), n); // untimed
+    if (cudaEventRecord(a, s) != cudaSuccess)
+        st = KPP_ERR_CUDA;
+    for (int r = 0; st == KPP_OK && r < reps; ++r)
+        read_kernel<<<grid, kReadThreads, 0, s>>>(reinterpret_cast<const uint4 *>(buf), n);
+    if (st == KPP_OK && (cudaGetLastError() != cudaSuccess || cudaEventRecord(b, s) != cudaSuccess))
+        st = KPP_ERR_LAUNCH;
+    float ms = 0.f;
+    if (st == KPP_OK &&
+        (cudaEventSynchronize(b) != cudaSuccess || cudaEventElapsedTime(&ms, a, b) != cudaSuccess))
+        st = KPP_ERR_CUDA;
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (st == KPP_OK)
+        *ms_out = ms / (float)reps;
+    return st;
+}

@@ -8,6 +8,8 @@
 // For them this entry point needs no workspace and allocates nothing: its
 // scratch is the file-scope device array below, which every GPU that loads
 // the library holds until the process exits.
+#include <cudaTypedefs.h>
+
 #include <cstring>
 #include <mutex>
 
@@ -26,9 +28,41 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratch
 
 // Device address of g_noalloc_scratch per device.  In host code the symbol
 // itself is only a host-side stand-in; the device address has to be asked
-// for with cudaGetSymbolAddress while that device is current.
+// for with cudaGetSymbolAddress while that device is current.  The address
+// is looked up on the first call on a device and kept together with the
+// context it belongs to: if that context is torn down and replaced (e.g. by
+// cudaDeviceReset), the module is loaded again at another address, so a
+// changed context triggers a fresh lookup.
 std::mutex g_mutex;
-void *g_scratch_ptr[64] = {};
+struct ScratchAddr {
+    CUcontext ctx;
+    void *ptr;
+};
+ScratchAddr g_scratch[64] = {};
+
+PFN_cuCtxGetCurrent_v4000 ctx_get_current()
+{
+    static std::once_flag once;
+    static PFN_cuCtxGetCurrent_v4000 fn = nullptr;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 4000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuCtxGetCurrent_v4000>(p);
+    });
+    return fn;
+}
+
+CUcontext current_context()
+{
+    auto fn = ctx_get_current();
+    CUcontext c = nullptr;
+    if (!fn || fn(&c) != CUDA_SUCCESS)
+        return nullptr;
+    return c;
+}
 
 kpp_status scratch_for_current_device(void **out)
 {
@@ -36,13 +70,15 @@ kpp_status scratch_for_current_device(void **out)
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64)
         return KPP_ERR_CUDA;
     std::lock_guard<std::mutex> lock(g_mutex);
-    if (!g_scratch_ptr[dev]) {
+    const CUcontext ctx = current_context();
+    if (!g_scratch[dev].ptr || !ctx || g_scratch[dev].ctx != ctx) {
         void *p = nullptr;
         if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p)
             return KPP_ERR_CUDA;
-        g_scratch_ptr[dev] = p;
+        g_scratch[dev].ptr = p;
+        g_scratch[dev].ctx = current_context(); // the lookup made the context current
     }
-    *out = g_scratch_ptr[dev];
+    *out = g_scratch[dev].ptr;
     return KPP_OK;
 }
 

@@ -91,7 +91,7 @@ __device__ __forceinline__ void seed_blocks(const Problem &p, const PersistArgs 
         if (b == 0)
             p.idx[0] = ci;
         if (p.K > 1)
-            ds.th[1] = thresh_for_u(philox_uniform(p.seed, p.stream_id, 1));
+            ds.th[1] = thresh_for_u(philox_uniform(p.seed, p.stream_id, 1), p.exact_draws);
     }
 
     for (int m = 0; m < p.K; ++m) {
@@ -176,7 +176,8 @@ __device__ __forceinline__ void seed_blocks(const Problem &p, const PersistArgs 
             // 32-row chunk sums (for the owner's search below)
             if (threadIdx.x == 32 && next + 1 < p.K)
                 ds.th[(next + 1) & 1] =
-                    thresh_for_u(philox_uniform(p.seed, p.stream_id, (uint64_t)(next + 1)));
+                    thresh_for_u(philox_uniform(p.seed, p.stream_id, (uint64_t)(next + 1)),
+                                 p.exact_draws);
             if (chunk_path && !forced) {
                 for (int c = threadIdx.x - 32; c < nchunks; c += blockDim.x - 32) {
                     const int64_t rb = r0 + 32ll * c;

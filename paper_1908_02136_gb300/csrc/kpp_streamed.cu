@@ -70,7 +70,7 @@ __device__ __forceinline__ void finish_pass(const Problem &p, int m, const Pair 
                                                 : philox_uniform(p.seed, p.stream_id, (uint64_t)next);
         const PFind r = warp_pfind(
             p.nblocks, [&](int k) { return Pair{stage_pairs[k].x, stage_pairs[k].y}; }, Pair{},
-            thresh_for_u(u), true);
+            thresh_for_u(u, p.exact_draws), true);
         if (lane == 0) {
             T_sh = (double)r.total.hi + (double)r.total.lo;
             th_sh = r.th;

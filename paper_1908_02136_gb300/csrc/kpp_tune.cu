@@ -91,6 +91,7 @@ bool tuned_options(int64_t N, int32_t d, int32_t K, int dt, const kpp_options &a
     *out = it->second;
     out->timeout_us = asked.timeout_us; // the caller's bound and graph choice stand
     out->use_graph = asked.use_graph;
+    out->exact_draws = asked.exact_draws;
     return true;
 }
 
