@@ -68,6 +68,10 @@ def parse():
                          "(comma list, or 'none')")
     ap.add_argument("--form-steps", type=int, default=3,
                     help="timed steps of each precision form beside the FP32 run")
+    ap.add_argument("--shard", default="replicas", choices=["replicas", "points"],
+                    help="N > 1 and one seeding workload: every rank seeds its own replica "
+                         "(weak scaling), or one problem is split by rows over the ranks "
+                         "(strong scaling)")
     ap.add_argument("--no-read-peaks", action="store_true",
                     help="skip the live pure-read bandwidth measurement")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -1076,6 +1080,85 @@ def run_seeding(args, rank, world, local, dev, pg, barrier):
         }), flush=True)
 
 
+def run_sharded_seeding(args, rank, world, local, dev, pg, barrier):
+    """--shard points: ONE problem of the workload split by rows over the
+    ranks (contiguous ranges, Algorithm 2's partition), each rank seeding its
+    range with kpp_shard_* and exchanging, per pass, the D^2 totals
+    (all-gather) and the new centre's row (sum all-reduce) over NCCL.  A step
+    is one whole seeding of the problem; strong scaling of the fixed problem."""
+    import torch
+
+    import paper_1908_02136_gb300 as kpp
+    from paper_1908_02136_gb300 import datagen, multi
+
+    wl = datagen.WORKLOADS[args.workload]
+    if args.n_points or args.k_seeds:
+        import dataclasses
+
+        n_, k_ = args.n_points or wl.N, args.k_seeds or wl.K
+        wl = dataclasses.replace(wl, N=n_, K=k_, name=f"{wl.name}@N{n_}K{k_}")
+    N, d, K = wl.N, wl.d, wl.K
+    lo, hi = multi.shard_rows(N, world)[rank]
+    x = (torch.from_numpy(datagen.workload_points(wl)).to(dev) if N <= 2_000_000
+         else datagen.workload_points(wl, dev))
+    mine = x[lo:hi].clone()  # this rank's rows only
+    del x
+    torch.cuda.empty_cache()
+    comm = multi.ProcessGroupComm(pg) if pg is not None else multi.InProcessComm()
+    shard = kpp.PointShard(mine, lo, N, K, wl.draw_seed, 0, rank, world)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    for _ in range(args.warmup):
+        flush.fill_(1)
+        multi.seed_sharded([shard], comm, K)
+    torch.cuda.synchronize(dev)
+    st = shard.status()
+    if st != kpp.OK:
+        raise kpp.KppError(st, "sharded warmup")
+    barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    for s_ in range(args.steps):
+        flush.fill_(s_ & 0xFF)
+        starts[s_].record(stream)
+        multi.seed_sharded([shard], comm, K)
+        ends[s_].record(stream)
+    torch.cuda.synchronize(dev)
+    clocks = sampler.stop()
+    barrier()
+    step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
+    total_ms = multi.max_over_ranks(sum(step_ms), pg, dev)
+    ms = total_ms / args.steps
+    idx = shard.idx.cpu().numpy()
+    assert (idx >= 0).all() and (idx < N).all() and len(set(idx.tolist())) == K
+    peaks = measured_peaks()
+    peak = peaks["hbm_gbs"] if peaks else 6800.0
+    per_pass = (hi - lo) * d * 4 + 8 * (hi - lo)  # this rank's points and D^2
+    achieved = per_pass * K / (ms / 1e3) / 1e9
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": float(N) * K * d / (ms / 1e3), "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": wl.name, "N": N, "d": d, "K": K, "form": "sharded",
+                       "parallelism": f"points split over {world} ranks (contiguous rows)",
+                       "rows_on_rank0": hi - lo,
+                       "l2": "flushed between steps (512 MiB write)"},
+            "clocks": clocks, "e2e": None,
+            # per pass: the pass, the pick (not after the last), plus the first seed and phi
+            "gpu_launches": args.steps * (2 * K + 1),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "kernel": "streamed pass kernel (per rank)",
+                         "algorithmic_bytes_per_pass_rank0": per_pass},
+            "cpu_baseline": None,
+        }), flush=True)
+
+
 def oracle_baseline(stored, scales, K, seed, stream_id, budget_s: float = 15.0):
     """The multi-threaded FP64 oracle on all host cores, on the workload's
     stored points, for as many of the K passes as fit about `budget_s`
@@ -1132,7 +1215,10 @@ def main():
     if args.workload.startswith(KMPAR_PREFIX):
         run_kmpar(args, rank, world, dev, pg, barrier)
         return
-    run_seeding(args, rank, world, local, dev, pg, barrier)
+    if args.shard == "points":
+        run_sharded_seeding(args, rank, world, local, dev, pg, barrier)
+    else:
+        run_seeding(args, rank, world, local, dev, pg, barrier)
     if pg is not None:
         pg.destroy_process_group()
 

@@ -221,10 +221,11 @@ KPP_API kpp_status kpp_quantize(const float *x, int64_t N, int32_t d, kpp_dtype 
  * Measurement utility (not part of the method; the paper has no
  * counterpart): the rate at which this GPU streams reads from a buffer, the
  * denominator a seeding pass -- a pure read stream over the points -- is
- * compared with.  Reads `bytes` of `buf` once untimed, then `reps` times,
- * with one full wave of resident CTAs issuing 16-byte loads, timed with CUDA
- * events on `stream`; *ms_out (host) receives the mean milliseconds per
- * timed sweep.  A buffer far larger than L2 gives the HBM read bandwidth; a
+ * compared with.  Reads `bytes` of `buf` once untimed, then `reps` times in
+ * one launch, with one full wave of resident CTAs each reading its own
+ * contiguous share with 16-byte loads (as a seeding CTA reads its row
+ * block), timed with CUDA events on `stream`; *ms_out (host) receives the
+ * mean milliseconds per timed sweep.  A buffer far larger than L2 gives the HBM read bandwidth; a
  * buffer well inside L2, read again and again, the L2 read bandwidth.
  *   buf    device, 16-byte aligned; bytes a multiple of 16 (>= 16)
  *   reps   >= 1
@@ -399,6 +400,73 @@ KPP_API kpp_status kpp_kmeans_par(const float *points, int64_t N, int32_t d, int
                                   int64_t *n_cand_out, int64_t *weights_out, int32_t *labels_out,
                                   float *d2_out, double *phi_out, void *workspace,
                                   size_t workspace_bytes, kpp_stream_t stream);
+
+/*
+ * Point-sharded seeding of one problem over several processes (one GPU
+ * each): Algorithm 2's partition of the points into N_1 .. N_l, with each
+ * process holding one contiguous range of rows.  Contiguous ranges keep the
+ * index order of the inverse-CDF draw, so the result is the single-GPU
+ * seeding's (bit-identical on data whose sums are exact).  Per pass the
+ * processes exchange two small messages, which the caller carries with its
+ * own collectives (e.g. NCCL through torch.distributed):
+ *
+ *   kpp_shard_first(s, X)                   first seed's row into X (owner) or 0s
+ *   sum-all-reduce X over the processes    (int64 words)
+ *   for m = 0 .. K-1:
+ *     kpp_shard_pass(s, m, X, total)        D^2 update; this shard's total
+ *     all-gather `total` into totals        (world x 2 floats, rank order)
+ *     if m < K-1:
+ *       kpp_shard_pick(s, m, totals, X)     draw of seed m+1: its owner writes
+ *       sum-all-reduce X                    its row into X, the others 0s
+ *   kpp_shard_phi(totals, world, phi)       phi from the last totals
+ *
+ * Every call is asynchronous on `stream`; nothing waits on the host between
+ * passes.  The draw: every process finds, from the gathered totals, the rank
+ * whose running total passes t = u * T (the same FP32-pair arithmetic on the
+ * same values everywhere); that rank narrows t to a block, a warp segment and
+ * a row of its own D^2 as kpp_seed's streamed form does.  T = 0 before K
+ * seeds stops every process alike (indices -1, status KPP_ERR_DEGENERATE);
+ * kpp_read_status(s->workspace, stream) reads a process's status.
+ */
+typedef struct {
+    const void *points;       /* [n_local x d] this process's rows, 16-byte aligned */
+    const float *row_scales;  /* [n_local] FP8 only, else NULL */
+    int64_t row0;             /* global index of the first local row */
+    int64_t n_local;          /* >= 1 */
+    int64_t n_global;         /* rows over all processes, < 2^31 */
+    int32_t d;                /* 1 <= d <= 4096 */
+    int32_t K;                /* 1 <= K <= n_global */
+    int32_t dtype;            /* kpp_dtype */
+    int32_t rank, world;      /* 0 <= rank < world <= 1024; ranges in rank order */
+    uint64_t seed, stream_id; /* Philox key of the draws, as kpp_seed */
+    int64_t *indices_out;     /* [K] device: the global indices (on every process) */
+    float *d2_out;            /* [n_local] device: this process's D^2 */
+    void *workspace;          /* >= kpp_shard_workspace_size bytes, 256-byte aligned */
+    size_t workspace_bytes;
+} kpp_shard;
+
+/* 64-bit words of the exchange buffer X for rows of d values of `dtype`
+ * (the centre's global index, its FP8 scale and its stored row). */
+KPP_API int64_t kpp_shard_exchange_words(int32_t d, kpp_dtype dtype);
+/* Workspace bytes of one process (0 if the descriptor is invalid). */
+KPP_API size_t kpp_shard_workspace_size(const kpp_shard *s, const kpp_options *opts);
+/* X: [kpp_shard_exchange_words] int64 device, 16-byte aligned.  Also resets
+ * the workspace's status. */
+KPP_API kpp_status kpp_shard_first(const kpp_shard *s, int64_t *exchange, kpp_stream_t stream);
+/* Pass m with the centre in X (after the sum-all-reduce): writes
+ * indices_out[m], updates d2_out, and writes this shard's D^2 sum as an FP32
+ * pair (hi, lo) to total_out[0..1] (device). */
+KPP_API kpp_status kpp_shard_pass(const kpp_shard *s, int32_t m, const int64_t *exchange,
+                                  float *total_out, kpp_stream_t stream,
+                                  const kpp_options *opts);
+/* The draw after pass m < K-1 from all_totals [world x 2] (device, rank
+ * order): writes X (the owner's row, zeros elsewhere). */
+KPP_API kpp_status kpp_shard_pick(const kpp_shard *s, int32_t m, const float *all_totals,
+                                  int64_t *exchange, kpp_stream_t stream,
+                                  const kpp_options *opts);
+/* phi_out [1] FP64 device: the sum of the last gathered totals. */
+KPP_API kpp_status kpp_shard_phi(const float *all_totals, int32_t world, double *phi_out,
+                                 kpp_stream_t stream);
 
 /*
  * Seeding for callers that cannot allocate device memory.  (The paper has

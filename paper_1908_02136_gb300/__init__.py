@@ -78,6 +78,18 @@ _lock = threading.Lock()
 _lib = None
 
 
+class Shard(ctypes.Structure):
+    """Mirror of kpp_shard (one process's rows of a point-sharded problem)."""
+
+    _fields_ = [("points", ctypes.c_void_p), ("row_scales", ctypes.c_void_p),
+                ("row0", ctypes.c_int64), ("n_local", ctypes.c_int64),
+                ("n_global", ctypes.c_int64), ("d", ctypes.c_int32), ("K", ctypes.c_int32),
+                ("dtype", ctypes.c_int32), ("rank", ctypes.c_int32), ("world", ctypes.c_int32),
+                ("seed", ctypes.c_uint64), ("stream_id", ctypes.c_uint64),
+                ("indices_out", ctypes.c_void_p), ("d2_out", ctypes.c_void_p),
+                ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_size_t)]
+
+
 def library_path() -> str:
     return _build.LIB
 
@@ -120,6 +132,18 @@ def load_library(build_if_stale: bool = True):
         lib.kpp_quantize.restype = ctypes.c_int
         lib.kpp_measure_read.argtypes = [P, ctypes.c_size_t, I32, P, P]
         lib.kpp_measure_read.restype = ctypes.c_int
+        lib.kpp_shard_exchange_words.argtypes = [I32, ctypes.c_int]
+        lib.kpp_shard_exchange_words.restype = I64
+        lib.kpp_shard_workspace_size.argtypes = [P, P]
+        lib.kpp_shard_workspace_size.restype = ctypes.c_size_t
+        lib.kpp_shard_first.argtypes = [P, P, P]
+        lib.kpp_shard_first.restype = ctypes.c_int
+        lib.kpp_shard_pass.argtypes = [P, I32, P, P, P, P]
+        lib.kpp_shard_pass.restype = ctypes.c_int
+        lib.kpp_shard_pick.argtypes = [P, I32, P, P, P, P]
+        lib.kpp_shard_pick.restype = ctypes.c_int
+        lib.kpp_shard_phi.argtypes = [P, I32, P, P]
+        lib.kpp_shard_phi.restype = ctypes.c_int
         lib.kpp_tune_workspace_size.argtypes = [I64, I32, I32, ctypes.c_int]
         lib.kpp_tune_workspace_size.restype = ctypes.c_size_t
         lib.kpp_tune.argtypes = [P, P, I64, I32, I32, ctypes.c_int, P, P, P, ctypes.c_size_t, P,
@@ -241,6 +265,97 @@ def measure_read_gbs(nbytes: int, reps: int, device="cuda") -> float:
     if st != OK:
         raise KppError(st, "kpp_measure_read")
     return buf.numel() * 4 / (ms.value * 1e-3) / 1e9
+
+
+def kpp_shard_exchange_words(d, dtype) -> int:
+    return load_library().kpp_shard_exchange_words(d, dtype)
+
+
+def kpp_shard_workspace_size(shard, opts=None) -> int:
+    return load_library().kpp_shard_workspace_size(ctypes.byref(shard), _opts_ptr(opts))
+
+
+def kpp_shard_first(shard, exchange, stream) -> int:
+    return load_library().kpp_shard_first(ctypes.byref(shard), exchange, stream)
+
+
+def kpp_shard_pass(shard, m, exchange, total_out, stream, opts=None) -> int:
+    return load_library().kpp_shard_pass(ctypes.byref(shard), m, exchange, total_out, stream,
+                                         _opts_ptr(opts))
+
+
+def kpp_shard_pick(shard, m, all_totals, exchange, stream, opts=None) -> int:
+    return load_library().kpp_shard_pick(ctypes.byref(shard), m, all_totals, exchange, stream,
+                                         _opts_ptr(opts))
+
+
+def kpp_shard_phi(all_totals, world, phi_out, stream) -> int:
+    return load_library().kpp_shard_phi(all_totals, world, phi_out, stream)
+
+
+class PointShard:
+    """One shard (a contiguous range of rows) of a point-sharded seeding, on
+    the points' GPU, driven by ``multi.seed_sharded``.
+
+    ``points``: this shard's rows [n_local, d] (CUDA, stored as ``dtype``);
+    ``row0``: the global index of its first row; ``n_global``: the rows of
+    all shards.  Holds the buffers the exchanges carry: ``exchange`` (int64,
+    summed over shards), ``total`` (2 floats, gathered into ``totals``).
+    After the seeding: ``idx`` (global indices), ``d2`` (this shard's D^2),
+    ``phi``; ``status()`` reads the device status.
+    """
+
+    def __init__(self, points, row0: int, n_global: int, K: int, seed: int, stream_id: int,
+                 rank: int, world: int, *, dtype=None, row_scales=None, opts=None):
+        import torch
+
+        n, d = points.shape
+        dt = _dtype_code(points, dtype)
+        dev = points.device
+        self.points, self.row_scales, self.opts, self.world = points, row_scales, opts, world
+        self.idx = torch.full((K,), -1, dtype=torch.int64, device=dev)
+        self.d2 = torch.empty(n, dtype=torch.float32, device=dev)
+        self.phi = torch.zeros(1, dtype=torch.float64, device=dev)
+        self.total = torch.zeros(2, dtype=torch.float32, device=dev)
+        self.totals = torch.zeros(2 * world, dtype=torch.float32, device=dev)
+        words = kpp_shard_exchange_words(d, dt)
+        if words <= 0:
+            raise KppError(ERR_INVALID_ARG, "kpp_shard_exchange_words")
+        self.exchange = torch.zeros(words, dtype=torch.int64, device=dev)
+        self.desc = Shard(points.data_ptr(), None if row_scales is None else row_scales.data_ptr(),
+                          row0, n, n_global, d, K, dt, rank, world, seed, stream_id,
+                          self.idx.data_ptr(), self.d2.data_ptr(), None, 0)
+        with torch.cuda.device(dev):
+            nb = kpp_shard_workspace_size(self.desc, opts)
+        if nb == 0:
+            raise KppError(ERR_INVALID_ARG, "kpp_shard_workspace_size")
+        self.ws = torch.empty(nb, dtype=torch.uint8, device=dev)
+        self.desc.workspace, self.desc.workspace_bytes = self.ws.data_ptr(), nb
+        self.dev = dev
+
+    def _check(self, st, where):
+        if st != OK:
+            raise KppError(st, where)
+
+    def first(self):
+        self._check(kpp_shard_first(self.desc, self.exchange.data_ptr(),
+                                    _stream_handle(self.dev)), "kpp_shard_first")
+
+    def local_pass(self, m: int):
+        self._check(kpp_shard_pass(self.desc, m, self.exchange.data_ptr(), self.total.data_ptr(),
+                                   _stream_handle(self.dev), self.opts), "kpp_shard_pass")
+
+    def pick(self, m: int):
+        self._check(kpp_shard_pick(self.desc, m, self.totals.data_ptr(),
+                                   self.exchange.data_ptr(), _stream_handle(self.dev), self.opts),
+                    "kpp_shard_pick")
+
+    def finish(self):
+        self._check(kpp_shard_phi(self.totals.data_ptr(), self.world, self.phi.data_ptr(),
+                                  _stream_handle(self.dev)), "kpp_shard_phi")
+
+    def status(self) -> int:
+        return kpp_read_status(self.ws.data_ptr(), _stream_handle(self.dev))
 
 
 def kpp_tune_workspace_size(N, d, K, dtype) -> int:

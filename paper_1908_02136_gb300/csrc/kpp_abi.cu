@@ -465,6 +465,144 @@ kpp_status kpp_seed(const void *points, const float *row_scales, int64_t N, int3
     return run_streamed(pl, p, s, use_graph);
 }
 
+// ---------------------------------------------------------------------------
+// Point-sharded seeding (one contiguous row range of a problem per process).
+// ---------------------------------------------------------------------------
+static bool shard_ok(const kpp_shard *s)
+{
+    return s && s->points && aligned(s->points, 16) && s->indices_out && s->d2_out &&
+           s->n_local >= 1 && s->row0 >= 0 && s->n_global < (int64_t(1) << 31) &&
+           s->row0 + s->n_local <= s->n_global && s->d >= 1 && s->d <= kMaxDim && s->K >= 1 &&
+           s->K <= s->n_global && s->dtype >= KPP_F32 && s->dtype <= KPP_FP8_E4M3 &&
+           s->world >= 1 && s->world <= kStage && s->rank >= 0 && s->rank < s->world &&
+           ((s->dtype == KPP_FP8_E4M3) == (s->row_scales != nullptr));
+}
+
+// The shard's streamed plan and its Problem record.
+static kpp_status shard_problem(const kpp_shard *s, const kpp_options *opts, Plan *pl,
+                                Problem *p)
+{
+    if (!shard_ok(s))
+        return KPP_ERR_INVALID_ARG;
+    kpp_options o;
+    std::memset(&o, 0, sizeof(o));
+    if (opts)
+        o = *opts;
+    const int sms = device_sms();
+    if (sms <= 0)
+        return KPP_ERR_CUDA;
+    const kpp_status st = plan_streamed(s->n_local, s->d, s->dtype, o, sms, pl);
+    if (st != KPP_OK)
+        return st;
+    if (!s->workspace || !aligned(s->workspace, kAlign) || s->workspace_bytes < pl->ws_bytes)
+        return KPP_ERR_WORKSPACE;
+    std::memset(p, 0, sizeof(*p));
+    p->points = s->points;
+    p->scales = s->row_scales;
+    p->N = s->n_local;
+    p->d = s->d;
+    p->K = s->K;
+    p->seed = s->seed;
+    p->stream_id = s->stream_id;
+    p->nblocks = pl->nblocks;
+    p->chunk = pl->chunk;
+    p->nseg = pl->nseg;
+    p->sw = pl->sw;
+    p->idx = s->indices_out;
+    p->d2 = s->d2_out;
+    char *ws = reinterpret_cast<char *>(s->workspace);
+    p->ctl = reinterpret_cast<Control *>(ws);
+    p->block_sums = reinterpret_cast<float2 *>(ws + pl->off_bsum);
+    p->seg_sums = reinterpret_cast<float2 *>(ws + pl->off_seg);
+    p->n_global = s->n_global;
+    p->exact_draws = (opts && opts->exact_draws) ? 1 : 0;
+    return KPP_OK;
+}
+
+int64_t kpp_shard_exchange_words(int32_t d, kpp_dtype dtype)
+{
+    if (d < 1 || d > kMaxDim || (int)dtype < KPP_F32 || (int)dtype > KPP_FP8_E4M3)
+        return 0;
+    return xchg_words(d, elem_bytes((int)dtype));
+}
+
+size_t kpp_shard_workspace_size(const kpp_shard *s, const kpp_options *opts)
+{
+    Plan pl;
+    kpp_options o;
+    std::memset(&o, 0, sizeof(o));
+    if (opts)
+        o = *opts;
+    const int sms = device_sms();
+    if (!shard_ok(s) || sms <= 0 || plan_streamed(s->n_local, s->d, s->dtype, o, sms, &pl) != KPP_OK)
+        return 0;
+    return pl.ws_bytes;
+}
+
+kpp_status kpp_shard_first(const kpp_shard *s, int64_t *exchange, kpp_stream_t stream)
+{
+    Plan pl;
+    Problem p;
+    const kpp_status st = shard_problem(s, nullptr, &pl, &p);
+    if (st != KPP_OK)
+        return st;
+    if (!exchange || !aligned(exchange, 16))
+        return KPP_ERR_INVALID_ARG;
+    cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+    if (cudaMemsetAsync(p.ctl, 0, sizeof(Control), cs) != cudaSuccess)
+        return KPP_ERR_CUDA;
+    return shard_first_launch(p, s->row0, reinterpret_cast<long long *>(exchange),
+                              elem_bytes(s->dtype), cs) == cudaSuccess
+               ? KPP_OK
+               : KPP_ERR_LAUNCH;
+}
+
+kpp_status kpp_shard_pass(const kpp_shard *s, int32_t m, const int64_t *exchange,
+                          float *total_out, kpp_stream_t stream, const kpp_options *opts)
+{
+    Plan pl;
+    Problem p;
+    const kpp_status st = shard_problem(s, opts, &pl, &p);
+    if (st != KPP_OK)
+        return st;
+    if (!exchange || !aligned(exchange, 16) || !total_out || m < 0 || m >= s->K)
+        return KPP_ERR_INVALID_ARG;
+    p.xchg = reinterpret_cast<const long long *>(exchange);
+    p.shard_total = total_out;
+    return streamed_launch(pl.sk, pl.grid, p, m, reinterpret_cast<cudaStream_t>(stream)) ==
+                   cudaSuccess
+               ? KPP_OK
+               : KPP_ERR_LAUNCH;
+}
+
+kpp_status kpp_shard_pick(const kpp_shard *s, int32_t m, const float *all_totals,
+                          int64_t *exchange, kpp_stream_t stream, const kpp_options *opts)
+{
+    Plan pl;
+    Problem p;
+    const kpp_status st = shard_problem(s, opts, &pl, &p);
+    if (st != KPP_OK)
+        return st;
+    if (!exchange || !aligned(exchange, 16) || !all_totals || m < 0 || m >= s->K - 1)
+        return KPP_ERR_INVALID_ARG;
+    return shard_pick_launch(p, m, s->rank, s->world, all_totals, s->row0,
+                             reinterpret_cast<long long *>(exchange), elem_bytes(s->dtype),
+                             reinterpret_cast<cudaStream_t>(stream)) == cudaSuccess
+               ? KPP_OK
+               : KPP_ERR_LAUNCH;
+}
+
+kpp_status kpp_shard_phi(const float *all_totals, int32_t world, double *phi_out,
+                         kpp_stream_t stream)
+{
+    if (!all_totals || !phi_out || world < 1 || world > kStage)
+        return KPP_ERR_INVALID_ARG;
+    return shard_phi_launch(all_totals, world, phi_out, reinterpret_cast<cudaStream_t>(stream)) ==
+                   cudaSuccess
+               ? KPP_OK
+               : KPP_ERR_LAUNCH;
+}
+
 kpp_status kpp_read_status(const void *workspace, kpp_stream_t stream)
 {
     if (!workspace)

@@ -56,7 +56,23 @@ struct Problem {
     unsigned long long *mail;  // persistent form: the drawn index, tagged with its pass
     int32_t recompute;         // streamed form: every pass rebuilds D^2 from all chosen seeds
     int32_t exact_draws;       // every draw decision in FP64 (the near-tie path), for testing
+    // point-sharded seeding (one contiguous row range of a larger problem):
+    // the centre of the pass comes from the exchange buffer `xchg` (global
+    // index, row scale, stored row), indices are global (< n_global), and a
+    // pass ends with the shard's D^2 total in `shard_total` instead of a draw
+    const long long *xchg;
+    float *shard_total;
+    int64_t n_global;
 };
+
+// Exchange buffer of point-sharded seeding, in 64-bit words: [0] the global
+// index of the centre, [1] its FP8 row scale (low 32 bits), [2..] its stored
+// row (d * bytes, padded to 16 bytes).  Sharded processes sum their buffers
+// (the owner's words plus zeros), so every word is its owner's bit pattern.
+__host__ __device__ __forceinline__ int64_t xchg_words(int d, int elem_bytes)
+{
+    return 2 + 2 * (((int64_t)d * elem_bytes + 15) / 16);
+}
 
 // ---------------------------------------------------------------------------
 // Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two 64x64

@@ -22,6 +22,12 @@ int streamed_segments();
 size_t streamed_smem(const StreamedKernel &k, int d);
 cudaError_t streamed_launch(const StreamedKernel &k, int grid, const Problem &p, int m,
                             cudaStream_t stream);
+// Point-sharded seeding (kpp_shard_*): first seed, draw after a pass, phi.
+cudaError_t shard_first_launch(const Problem &p, int64_t row0, long long *xchg, int eb,
+                               cudaStream_t stream);
+cudaError_t shard_pick_launch(const Problem &p, int m, int rank, int world, const float *totals,
+                              int64_t row0, long long *xchg, int eb, cudaStream_t stream);
+cudaError_t shard_phi_launch(const float *totals, int world, double *phi, cudaStream_t stream);
 
 // Runtime arguments of the persistent kernel.
 struct PersistArgs {

@@ -18,24 +18,33 @@ constexpr int kReadUnroll = 8;
 // never happens.
 __device__ uint32_t g_read_sink;
 
-__global__ void __launch_bounds__(kReadThreads) read_kernel(const uint4 *buf, int64_t n)
+// Each CTA reads one contiguous share of the buffer (as a seeding CTA reads
+// its row block), `reps` times in one launch, so that every CTA stays on its
+// SM from one sweep to the next -- what a small buffer left in the L2 slices
+// near that SM is then read from there, as in the persistent seeding form.
+__global__ void __launch_bounds__(kReadThreads) read_kernel(const uint4 *buf, int64_t n, int reps)
 {
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t per = (n + gridDim.x - 1) / gridDim.x;
+    const int64_t b = (int64_t)blockIdx.x * per;
+    const int64_t e = (b + per) < n ? (b + per) : n;
+    const int64_t stride = blockDim.x;
     uint32_t acc = 0;
-    // kReadUnroll independent 16-byte loads in flight per thread
-    for (; i + (kReadUnroll - 1) * stride < n; i += kReadUnroll * stride) {
-        uint4 v[kReadUnroll];
+    for (int r = 0; r < reps; ++r) {
+        int64_t i = b + threadIdx.x;
+        // kReadUnroll independent 16-byte loads in flight per thread
+        for (; i + (kReadUnroll - 1) * stride < e; i += kReadUnroll * stride) {
+            uint4 v[kReadUnroll];
 #pragma unroll
-        for (int u = 0; u < kReadUnroll; ++u)
-            v[u] = ld_stream16(buf + i + u * stride);
+            for (int u = 0; u < kReadUnroll; ++u)
+                v[u] = ld_stream16(buf + i + u * stride);
 #pragma unroll
-        for (int u = 0; u < kReadUnroll; ++u)
-            acc ^= v[u].x ^ v[u].y ^ v[u].z ^ v[u].w;
-    }
-    for (; i < n; i += stride) {
-        const uint4 v = ld_stream16(buf + i);
-        acc ^= v.x ^ v.y ^ v.z ^ v.w;
+            for (int u = 0; u < kReadUnroll; ++u)
+                acc ^= v[u].x ^ v[u].y ^ v[u].z ^ v[u].w;
+        }
+        for (; i < e; i += stride) {
+            const uint4 v = ld_stream16(buf + i);
+            acc ^= v.x ^ v.y ^ v.z ^ v.w;
+        }
     }
     if (acc == 0x9e3779b9u)
         g_read_sink = acc;
@@ -70,11 +79,12 @@ extern "C" kpp_status kpp_measure_read(const void *buf, size_t bytes, int32_t re
         return KPP_ERR_CUDA;
     }
     kpp_status st = KPP_OK;
-    read_kernel<<<grid, kReadThreads, 0, s>>>(reinterpret_cast<const uint4 *>(buf), n); // untimed
+    const uint4 *v = reinterpret_cast<const uint4 *>(buf);
+    read_kernel<<<grid, kReadThreads, 0, s>>>(v, n, 1); // untimed: brings a small buffer into L2
     if (cudaEventRecord(a, s) != cudaSuccess)
         st = KPP_ERR_CUDA;
-    for (int r = 0; st == KPP_OK && r < reps; ++r)
-        read_kernel<<<grid, kReadThreads, 0, s>>>(reinterpret_cast<const uint4 *>(buf), n);
+    if (st == KPP_OK)
+        read_kernel<<<grid, kReadThreads, 0, s>>>(v, n, reps);
     if (st == KPP_OK && (cudaGetLastError() != cudaSuccess || cudaEventRecord(b, s) != cudaSuccess))
         st = KPP_ERR_LAUNCH;
     float ms = 0.f;

@@ -14,11 +14,23 @@ namespace kpp {
 
 constexpr int kStreamThreads = 256;
 
-// Returns the centre of pass m, or -1 if the kernel must stop.
+// Returns the centre of pass m, or -1 if the kernel must stop.  A sharded
+// pass takes it from the exchange buffer (a global index) and records it.
 __device__ __forceinline__ int64_t pass_centre(const Problem &p, int m)
 {
     if (*(volatile int32_t *)&p.ctl->status != KPP_OK)
         return -1;
+    if (p.xchg) {
+        const int64_t ci = (int64_t)__ldcg(p.xchg);
+        if (ci < 0 || ci >= p.n_global) {
+            if (threadIdx.x == 0 && blockIdx.x == 0)
+                atomicCAS(&p.ctl->status, KPP_OK, KPP_ERR_INVALID_ARG);
+            return -1;
+        }
+        if (blockIdx.x == 0 && threadIdx.x == 0)
+            p.idx[m] = ci;
+        return ci;
+    }
     int64_t ci = (m == 0) ? first_seed(p) : __ldcg(p.idx + m);
     if (ci < 0 || ci >= p.N) {
         if (threadIdx.x == 0 && blockIdx.x == 0)
@@ -62,6 +74,19 @@ __device__ __forceinline__ void finish_pass(const Problem &p, int m, const Pair 
     for (int k = threadIdx.x; k < p.nblocks; k += blockDim.x)
         stage_pairs[k] = __ldcg(p.block_sums + k);
     __syncthreads();
+    if (p.shard_total) { // sharded pass: the shard's total, no draw here
+        if (warp == 0) {
+            const PFind r = warp_pfind(
+                p.nblocks, [&](int k) { return Pair{stage_pairs[k].x, stage_pairs[k].y}; },
+                Pair{}, thresh_inf(), false);
+            if (lane == 0) {
+                p.shard_total[0] = r.total.hi;
+                p.shard_total[1] = r.total.lo;
+                p.ctl->ticket = 0u;
+            }
+        }
+        return;
+    }
     const bool final_pass = (m == p.K - 1);
     const int next = m + 1;
     const bool forced = !final_pass && next < p.n_forced;
@@ -158,7 +183,10 @@ __global__ void __launch_bounds__(kStreamThreads)
     for (int j = p.recompute ? 0 : m; j <= m; ++j) {
         const int64_t cj = (j == m) ? ci : __ldcg(p.idx + j);
         CentreRegs<DT, D, L> cr;
-        cr.load(p.points, p.scales, cj);
+        if (p.xchg) // the centre row as the exchange buffer carries it
+            cr.load(p.xchg + 2, reinterpret_cast<const float *>(p.xchg + 1), 0);
+        else
+            cr.load(p.points, p.scales, cj);
         io.first = (j == 0);
         w = pass_rows<DT, D, L, D2_INPLACE>(io, cr);
     }
@@ -184,12 +212,161 @@ __global__ void __launch_bounds__(kStreamThreads)
     for (int j = p.recompute ? 0 : m; j <= m; ++j) {
         const int64_t cj = (j == m) ? ci : __ldcg(p.idx + j);
         __syncthreads(); // the previous centre is no longer read
-        load_centre_smem<DT>(p.points, p.scales, cj, p.d, c_sh);
+        if (p.xchg)
+            load_centre_smem<DT>(p.xchg + 2, reinterpret_cast<const float *>(p.xchg + 1), 0, p.d,
+                                 c_sh);
+        else
+            load_centre_smem<DT>(p.points, p.scales, cj, p.d, c_sh);
         __syncthreads();
         io.first = (j == 0);
         w = pass_rows_generic<DT>(io, p.d, c_sh);
     }
     finish_pass(p, m, w);
+}
+
+// ---------------------------------------------------------------------------
+// Point-sharded seeding: one problem's rows split into contiguous ranges,
+// one per process (Algorithm 2's partition N_1..N_l across GPUs).  A process
+// holds rows [row0, row0 + p.N) of the n_global rows; between its passes the
+// processes gather their D^2 totals and sum their exchange buffers.
+// ---------------------------------------------------------------------------
+
+// Copies local row `r` (stored bytes and FP8 scale) of the shard into the
+// exchange buffer under global index `gidx`; all threads of the CTA take part.
+__device__ __forceinline__ void shard_put_row(const Problem &p, int64_t r, int64_t gidx,
+                                              long long *xchg, int eb)
+{
+    const int64_t rb = (int64_t)p.d * eb;
+    const unsigned char *src = reinterpret_cast<const unsigned char *>(p.points) + r * rb;
+    unsigned char *dst = reinterpret_cast<unsigned char *>(xchg + 2);
+    for (int64_t k = threadIdx.x; k < rb; k += blockDim.x)
+        dst[k] = src[k];
+    if (threadIdx.x == 0) {
+        xchg[0] = (long long)gidx;
+        xchg[1] = p.scales ? (long long)__float_as_uint(p.scales[r]) : 0ll;
+    }
+}
+
+__device__ __forceinline__ void zero_words(long long *w, int64_t n)
+{
+    for (int64_t k = threadIdx.x; k < n; k += blockDim.x)
+        w[k] = 0;
+}
+
+// The first seed, min(floor(u_0 * n_global), n_global - 1): the process
+// holding it writes its row, every other one zeros.
+__global__ void __launch_bounds__(kStreamThreads)
+    shard_first_kernel(Problem p, int64_t row0, long long *xchg, int64_t words, int eb)
+{
+    zero_words(xchg, words);
+    __syncthreads();
+    const double u = philox_uniform(p.seed, p.stream_id, 0);
+    int64_t i0 = (int64_t)floor(u * (double)p.n_global);
+    i0 = i0 < p.n_global - 1 ? i0 : p.n_global - 1;
+    if (i0 >= row0 && i0 < row0 + p.N)
+        shard_put_row(p, i0 - row0, i0, xchg, eb);
+}
+
+// The draw of seed m + 1 after pass m, given every process's D^2 total
+// (`totals`, world FP32 pairs in rank order, the same on every process):
+// every process finds the owner rank whose running total passes
+// t = u_{m+1} * T; the owner narrows it to a block, a warp segment and a row
+// of its own D^2 exactly as the single-GPU streamed form does, and writes the
+// row into the exchange buffer; the others write zeros.  T = 0 (fewer
+// distinct points than K) stops the seeding on every process alike.
+__global__ void __launch_bounds__(kStreamThreads)
+    shard_pick_kernel(Problem p, int m, int rank, int world, const float *totals, int64_t row0,
+                      long long *xchg, int64_t words, int eb)
+{
+    __shared__ Thresh th_sh;
+    __shared__ Pair before_sh;
+    __shared__ int64_t sel_sh, pick_sh;
+    __shared__ int degenerate_sh;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (*(volatile int32_t *)&p.ctl->status != KPP_OK)
+        return;
+    zero_words(xchg, words);
+    if (warp == 0) {
+        const double u = philox_uniform(p.seed, p.stream_id, (uint64_t)(m + 1));
+        const PFind r = warp_pfind(
+            world, [&](int k) { return Pair{totals[2 * k], totals[2 * k + 1]}; }, Pair{},
+            thresh_for_u(u, p.exact_draws), true);
+        if (lane == 0) {
+            degenerate_sh = !(r.total.hi > 0.f);
+            th_sh = r.th;
+            before_sh = r.before;
+            sel_sh = r.index;
+            if (r.index < 0) { // rounding left no rank above t: the last with weight
+                sel_sh = r.last_positive;
+                before_sh = Pair{};
+                th_sh.inf = 1;
+            }
+        }
+    }
+    __syncthreads();
+    if (degenerate_sh) {
+        if (threadIdx.x == 0) {
+            for (int k = m + 1; k < p.K; ++k)
+                p.idx[k] = -1;
+            atomicCAS(&p.ctl->status, KPP_OK, KPP_ERR_DEGENERATE);
+        }
+        return;
+    }
+    if (sel_sh != rank)
+        return;
+    if (warp == 0) {
+        // block, segment, row -- as the streamed form's own draw
+        Thresh th = th_sh;
+        PFind r = warp_pfind(
+            p.nblocks,
+            [&](int k) {
+                const float2 v = __ldcg(p.block_sums + k);
+                return Pair{v.x, v.y};
+            },
+            before_sh, th, false);
+        int64_t blk = r.index;
+        Pair before = r.before;
+        if (blk < 0) {
+            blk = r.last_positive >= 0 ? r.last_positive : 0;
+            before = before_sh;
+            th.inf = 1;
+        }
+        const float2 *segs = p.seg_sums + blk * (int64_t)p.nseg;
+        r = warp_pfind(
+            p.nseg,
+            [&](int k) {
+                const float2 v = __ldcg(segs + k);
+                return Pair{v.x, v.y};
+            },
+            before, th, false);
+        int64_t seg = r.index;
+        if (seg >= 0) {
+            before = r.before;
+        } else {
+            seg = r.last_positive >= 0 ? r.last_positive : 0;
+            th.inf = 1;
+        }
+        const int64_t rb0 = blk * p.chunk;
+        const int64_t rows_blk = (p.N - rb0) < p.chunk ? (p.N - rb0) : p.chunk;
+        int64_t first, last;
+        segment_rows(rb0, rows_blk, p.sw, p.nseg, (int)seg, &first, &last);
+        const int64_t pick = warp_rows_find(
+            first, last, [&](int64_t row) { return __ldcg(p.d2 + row); }, before, th);
+        if (lane == 0)
+            pick_sh = pick;
+    }
+    __syncthreads();
+    shard_put_row(p, pick_sh, row0 + pick_sh, xchg, eb);
+}
+
+// phi = the processes' final D^2 totals added in rank order (FP64 result).
+__global__ void shard_phi_kernel(const float *totals, int world, double *phi)
+{
+    const PFind r = warp_pfind(
+        world, [&](int k) { return Pair{totals[2 * k], totals[2 * k + 1]}; }, Pair{},
+        thresh_inf(), false);
+    if (threadIdx.x == 0)
+        phi[0] = (double)r.total.hi + (double)r.total.lo;
 }
 
 // ---------------------------------------------------------------------------
@@ -290,6 +467,27 @@ cudaError_t streamed_launch(const StreamedKernel &k, int grid, const Problem &p,
     void *args[] = {&pp, &mm};
     return cudaLaunchKernel(k.fn, dim3(grid), dim3(kStreamThreads), args, streamed_smem(k, p.d),
                             stream);
+}
+
+cudaError_t shard_first_launch(const Problem &p, int64_t row0, long long *xchg, int eb,
+                               cudaStream_t stream)
+{
+    shard_first_kernel<<<1, kStreamThreads, 0, stream>>>(p, row0, xchg, xchg_words(p.d, eb), eb);
+    return cudaGetLastError();
+}
+
+cudaError_t shard_pick_launch(const Problem &p, int m, int rank, int world, const float *totals,
+                              int64_t row0, long long *xchg, int eb, cudaStream_t stream)
+{
+    shard_pick_kernel<<<1, kStreamThreads, 0, stream>>>(p, m, rank, world, totals, row0, xchg,
+                                                        xchg_words(p.d, eb), eb);
+    return cudaGetLastError();
+}
+
+cudaError_t shard_phi_launch(const float *totals, int world, double *phi, cudaStream_t stream)
+{
+    shard_phi_kernel<<<1, 32, 0, stream>>>(totals, world, phi);
+    return cudaGetLastError();
 }
 
 } // namespace kpp

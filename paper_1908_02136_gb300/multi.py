@@ -70,3 +70,92 @@ def replica_stream(stream_id: int, rank: int, stride: int = 1 << 20) -> int:
     """Draw stream of rank ``rank``'s replica of a problem: distinct per rank,
     equal to ``stream_id`` on rank 0."""
     return stream_id + rank * stride
+
+
+# ---------------------------------------------------------------------------
+# One problem sharded by points (Algorithm 2's partition N_1 .. N_l, one
+# contiguous range of rows per GPU).  Per pass the shards exchange two small
+# messages: an all-gather of their D^2 totals (two floats each) and a sum of
+# their exchange buffers (the owner of the new centre contributes its row,
+# the others zeros).  No host synchronisation happens between passes.
+# ---------------------------------------------------------------------------
+
+
+def shard_rows(N: int, world: int):
+    """Contiguous row ranges [lo, hi) of ``world`` shards of N rows, in rank
+    order (the first N % world shards one row longer)."""
+    if world < 1 or N < world:
+        raise ValueError("need 1 <= world <= N")
+    base, extra = divmod(N, world)
+    out, lo = [], 0
+    for r in range(world):
+        hi = lo + base + (1 if r < extra else 0)
+        out.append((lo, hi))
+        lo = hi
+    return out
+
+
+def seed_sharded(shards, comm, K: int):
+    """The seeding of one problem over point shards.
+
+    ``shards``: the shards this process drives (one per process in a
+    multi-process run; all of them when every shard lives in this process),
+    each with ``first()``, ``local_pass(m)``, ``pick(m)``, ``finish()`` and the
+    buffers ``exchange`` (summed), ``total`` (gathered into ``totals``).
+    ``comm``: ``sum(buffers)`` and ``gather(parts, outs)`` over all shards.
+    """
+    for s in shards:
+        s.first()
+    comm.sum([s.exchange for s in shards])
+    for m in range(K):
+        for s in shards:
+            s.local_pass(m)
+        comm.gather([s.total for s in shards], [s.totals for s in shards])
+        if m < K - 1:
+            for s in shards:
+                s.pick(m)
+            comm.sum([s.exchange for s in shards])
+    for s in shards:
+        s.finish()
+
+
+class ProcessGroupComm:
+    """One shard per process: the exchanges as torch.distributed collectives
+    (NCCL between GPUs, gloo between CPU processes)."""
+
+    def __init__(self, dist, group=None):
+        self.dist = dist
+        self.group = group
+
+    def sum(self, bufs):
+        (b,) = bufs
+        self.dist.all_reduce(b, op=self.dist.ReduceOp.SUM, group=self.group)
+
+    def gather(self, parts, outs):
+        import torch
+
+        (p,), (o,) = parts, outs
+        world = self.dist.get_world_size(self.group)
+        got = [torch.empty_like(p) for _ in range(world)]
+        self.dist.all_gather(got, p, group=self.group)
+        o.copy_(torch.cat(got))
+
+
+class InProcessComm:
+    """Every shard in this process (e.g. several shards on one GPU): the same
+    exchanges as tensor copies -- the sum of the exchange buffers and the
+    concatenation of the totals in rank order."""
+
+    def sum(self, bufs):
+        total = bufs[0].clone()
+        for b in bufs[1:]:
+            total += b
+        for b in bufs:
+            b.copy_(total)
+
+    def gather(self, parts, outs):
+        import torch
+
+        g = torch.cat(list(parts))
+        for o in outs:
+            o.copy_(g)

@@ -33,7 +33,9 @@ def test_header_declares_the_boundary():
                      "kpp_seed_batched", "kpp_batch_workspace_size", "kpp_seed_noalloc",
                      "kpp_tune", "kpp_tune_workspace_size", "kpp_tune_clear",
                      "kpp_lloyd_workspace_size", "kpp_lloyd_prepare", "kpp_lloyd_step",
-                     "kpp_lloyd_assign", "kpp_kmeans_par_workspace_size", "kpp_kmeans_par"]:
+                     "kpp_lloyd_assign", "kpp_kmeans_par_workspace_size", "kpp_kmeans_par",
+                     "kpp_shard_exchange_words", "kpp_shard_workspace_size", "kpp_shard_first",
+                     "kpp_shard_pass", "kpp_shard_pick", "kpp_shard_phi", "kpp_measure_read"]:
         assert required in names
 
 
@@ -82,7 +84,7 @@ def test_invalid_arguments_fail_synchronously(lib):
 
 
 def test_ctypes_structs_match_the_header(tmp_path):
-    """The binding's kpp_options / kpp_plan mirror the C layout field by field."""
+    """The binding's struct mirrors follow the C layout field by field."""
     import ctypes
 
     import paper_1908_02136_gb300 as kpp
@@ -90,7 +92,7 @@ def test_ctypes_structs_match_the_header(tmp_path):
     src = tmp_path / "layout.c"
     lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "kpp.h"', "int main(void){"]
     for cname, py in (("kpp_options", kpp.Options), ("kpp_plan", kpp.Plan),
-                      ("kpp_problem", kpp.Problem)):
+                      ("kpp_problem", kpp.Problem), ("kpp_shard", kpp.Shard)):
         lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
         for f, _ in py._fields_:
             lines.append(f'printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
@@ -102,7 +104,7 @@ def test_ctypes_structs_match_the_header(tmp_path):
     out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
     got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
     for cname, py in (("kpp_options", kpp.Options), ("kpp_plan", kpp.Plan),
-                      ("kpp_problem", kpp.Problem)):
+                      ("kpp_problem", kpp.Problem), ("kpp_shard", kpp.Shard)):
         assert got[(cname, "size")] == ctypes.sizeof(py)
         for f, _ in py._fields_:
             assert got[(cname, f)] == getattr(py, f).offset, (cname, f)
