@@ -112,13 +112,12 @@ KERNEL_SOURCES = {
 
 
 def kernel_source_hash(kind: str = "persistent"):
-    """SHA-256 over one kernel's CUDA sources and the C header (to tell whether
-    a committed ncu traffic figure still describes the kernel being run)."""
+    """SHA-256 over one kernel's CUDA sources (to tell whether a committed ncu
+    traffic figure still describes the kernel being run)."""
     import hashlib
 
     h = hashlib.sha256()
     files = [os.path.join(ROOT, "paper_1908_02136_gb300", "csrc", f) for f in KERNEL_SOURCES[kind]]
-    files.append(os.path.join(ROOT, "include", "kpp.h"))
     for f in files:
         h.update(os.path.basename(f).encode())
         h.update(open(f, "rb").read())
@@ -959,7 +958,7 @@ def run_seeding(args, rank, world, local, dev, pg, barrier):
         assert np.all((idx_h >= 0) & (idx_h < N)) and len(set(idx_h.tolist())) == K
         assert float(d2[idx].abs().max()) == 0.0
         form_name = {kpp.FORM_STREAMED: "streamed", kpp.FORM_PERSISTENT: "persistent",
-                     kpp.FORM_RECOMPUTE: "recompute"}[plan["form"]]
+                     kpp.FORM_RECOMPUTE: "recompute", kpp.FORM_SMALL: "small"}[plan["form"]]
         return {"idx": idx, "d2": d2, "phi": phi, "ws": ws, "plan": plan, "form": form_name,
                 "tuned": tuned, "ms": total_ms / steps, "step_ms": step_ms,
                 "clocks": clocks, "steps": steps}

@@ -84,10 +84,15 @@ typedef enum {
     KPP_FORM_AUTO = 0,
     KPP_FORM_STREAMED = 1,   /* one kernel per seed, captured in a CUDA graph */
     KPP_FORM_PERSISTENT = 2, /* one cooperative launch for all K passes */
-    KPP_FORM_RECOMPUTE = 3   /* for comparison only: the paper's own step (Section II),
+    KPP_FORM_RECOMPUTE = 3,  /* for comparison only: the paper's own step (Section II),
                                 every pass recomputes each point's distance to all
                                 seeds chosen so far (O(N K^2 d) work) in the streamed
                                 form's launches; results identical to the streamed form */
+    KPP_FORM_SMALL = 4       /* one CTA of 1024 threads holds the points (as FP32, FP8 as
+                                its E4M3 values plus the row scales) and D^2 in shared
+                                memory for all K passes: 4 N (d + 1) bytes (+ 4 N for
+                                FP8) must fit one SM's shared memory; the automatic
+                                choice whenever they do */
 } kpp_form;
 
 /* Tuning knobs; a zeroed struct (or NULL) means "choose automatically". */
@@ -222,10 +227,11 @@ KPP_API kpp_status kpp_quantize(const float *x, int64_t N, int32_t d, kpp_dtype 
  * counterpart): the rate at which this GPU streams reads from a buffer, the
  * denominator a seeding pass -- a pure read stream over the points -- is
  * compared with.  Reads `bytes` of `buf` once untimed, then `reps` times in
- * one launch, with one full wave of resident CTAs each reading its own
- * contiguous share with 16-byte loads (as a seeding CTA reads its row
- * block), timed with CUDA events on `stream`; *ms_out (host) receives the
- * mean milliseconds per timed sweep.  A buffer far larger than L2 gives the HBM read bandwidth; a
+ * one launch of one full wave of resident CTAs (16-byte loads, every thread
+ * reading the same addresses in every sweep, so a CTA keeps its SM and its
+ * nearby L2 slices across sweeps, as the persistent seeding form does),
+ * timed with CUDA events on `stream`; *ms_out (host) receives the mean
+ * milliseconds per timed sweep.  A buffer far larger than L2 gives the HBM read bandwidth; a
  * buffer well inside L2, read again and again, the L2 read bandwidth.
  *   buf    device, 16-byte aligned; bytes a multiple of 16 (>= 16)
  *   reps   >= 1

@@ -26,7 +26,7 @@ import threading
 from . import build as _build
 
 F32, BF16, FP8_E4M3 = 0, 1, 2
-FORM_AUTO, FORM_STREAMED, FORM_PERSISTENT, FORM_RECOMPUTE = 0, 1, 2, 3
+FORM_AUTO, FORM_STREAMED, FORM_PERSISTENT, FORM_RECOMPUTE, FORM_SMALL = 0, 1, 2, 3, 4
 (OK, ERR_INVALID_ARG, ERR_CUDA, ERR_LAUNCH, ERR_TIMEOUT, ERR_DEGENERATE,
  ERR_WORKSPACE, ERR_UNSUPPORTED, ERR_CAPACITY) = range(9)
 

@@ -35,7 +35,7 @@ struct Plan {
     StreamedKernel sk;   // streamed form
     PersistentKernel pk; // persistent form
     const void *pfn;     // persistent kernel chosen (D^2 in smem or ping-pong)
-    size_t psmem;        // its dynamic shared memory
+    size_t psmem;        // its dynamic shared memory (also the small form's)
     PersistArgs pargs;
     int grid;      // CTAs per launch (== nblocks)
     int64_t chunk; // rows per CTA
@@ -99,6 +99,37 @@ kpp_status plan_streamed(int64_t N, int32_t d, int dt, const kpp_options &o, int
 
 kpp_status plan_persistent_at(int64_t N, int32_t K, const kpp_options &o, int sms, int per_sm,
                               Plan *pl);
+
+// The small form: one CTA, if the points and D^2 fit its shared memory.
+kpp_status plan_small(int64_t N, int32_t d, int dt, Plan *pl)
+{
+    int dev = 0, optin = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) !=
+            cudaSuccess)
+        return KPP_ERR_CUDA;
+    const void *fn = small_lookup(dt, d);
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, fn) != cudaSuccess)
+        return KPP_ERR_CUDA;
+    const size_t smem = small_smem(N, d, dt);
+    if (smem + fa.sharedSizeBytes > (size_t)optin)
+        return KPP_ERR_UNSUPPORTED; // does not fit one SM
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+        return KPP_ERR_CUDA;
+    pl->form = KPP_FORM_SMALL;
+    pl->pfn = fn;
+    pl->psmem = smem;
+    pl->chunk = N;
+    pl->nblocks = 1;
+    pl->grid = 1;
+    pl->nseg = small_threads() / 32;
+    pl->sw = 1;
+    pl->off_bsum = pl->off_seg = pl->off_slots = sizeof(Control);
+    pl->ws_bytes = sizeof(Control);
+    return KPP_OK;
+}
 
 // The persistent plan at the requested CTAs per SM, or fewer if that many
 // cannot be co-resident.
@@ -217,8 +248,13 @@ kpp_status make_plan(int64_t N, int32_t d, int32_t K, int dt, const kpp_options 
     }
     case KPP_FORM_PERSISTENT:
         return plan_persistent(N, d, K, dt, o, sms, pl);
+    case KPP_FORM_SMALL:
+        return plan_small(N, d, dt, pl);
     case KPP_FORM_AUTO: {
-        kpp_status st = plan_persistent(N, d, K, dt, o, sms, pl);
+        kpp_status st = plan_small(N, d, dt, pl);
+        if (st == KPP_OK || st == KPP_ERR_CUDA)
+            return st;
+        st = plan_persistent(N, d, K, dt, o, sms, pl);
         if (st == KPP_OK || st == KPP_ERR_INVALID_ARG || st == KPP_ERR_CUDA)
             return st;
         return plan_streamed(N, d, dt, o, sms, pl);
@@ -279,6 +315,13 @@ kpp_status run_persistent(const Plan &pl, const Problem &p, cudaStream_t stream)
     return persistent_launch(pl.pfn, pl.grid, pl.psmem, p, pl.pargs, stream) == cudaSuccess
                ? KPP_OK
                : KPP_ERR_LAUNCH;
+}
+
+kpp_status run_small(const Plan &pl, const Problem &p, cudaStream_t stream)
+{
+    if (cudaMemsetAsync(p.ctl, 0, sizeof(Control), stream) != cudaSuccess)
+        return KPP_ERR_CUDA;
+    return small_launch(pl.pfn, pl.psmem, p, stream) == cudaSuccess ? KPP_OK : KPP_ERR_LAUNCH;
 }
 
 kpp_status run_streamed(const Plan &pl, const Problem &p, cudaStream_t stream, int use_graph)
@@ -394,7 +437,13 @@ kpp_status kpp_describe(int64_t N, int32_t d, int32_t K, kpp_dtype dtype,
     plan->rows_per_cta = pl.chunk;
     plan->rows_per_segment = (pl.chunk + pl.nseg - 1) / pl.nseg;
     plan->workspace_bytes = (int64_t)pl.ws_bytes;
-    if (pl.form == KPP_FORM_PERSISTENT) {
+    if (pl.form == KPP_FORM_SMALL) {
+        plan->threads = small_threads();
+        plan->launches = 1;
+        plan->d2_in_smem = 1;
+        plan->cached_rows_per_cta = N;
+        plan->smem_bytes = (int64_t)pl.psmem;
+    } else if (pl.form == KPP_FORM_PERSISTENT) {
         plan->threads = persistent_threads();
         plan->launches = 1;
         plan->lanes_per_row = pl.pk.lanes;
@@ -461,6 +510,8 @@ kpp_status kpp_seed(const void *points, const float *row_scales, int64_t N, int3
     p.exact_draws = (opts && opts->exact_draws) ? 1 : 0;
     if (pl.form == KPP_FORM_PERSISTENT)
         return run_persistent(pl, p, s);
+    if (pl.form == KPP_FORM_SMALL)
+        return run_small(pl, p, s);
     const int use_graph = opts ? opts->use_graph : 0;
     return run_streamed(pl, p, s, use_graph);
 }

@@ -360,6 +360,20 @@ __device__ __forceinline__ Thresh thresh_for_u(double u, int exact = 0)
     return th;
 }
 
+// The same threshold from a draw whose float split was computed ahead.
+__device__ __forceinline__ Thresh thresh_for_split(double u, float uh, float ul, int exact = 0)
+{
+    Thresh th;
+    th.all_exact = exact;
+    th.u = u;
+    th.uh = uh;
+    th.ul = ul;
+    th.hi = th.lo = th.tol = 0.f;
+    th.T = Pair{0.f, 0.f};
+    th.inf = 0;
+    return th;
+}
+
 // Completes a threshold once T is known: t ~ uh*T.hi + (exact error of that
 // product) + uh*T.lo + ul*T.hi, all in FP32.
 __device__ __forceinline__ void thresh_set_total(Thresh &th, const Pair &T)

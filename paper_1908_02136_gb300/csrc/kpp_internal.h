@@ -29,6 +29,12 @@ cudaError_t shard_pick_launch(const Problem &p, int m, int rank, int world, cons
                               int64_t row0, long long *xchg, int eb, cudaStream_t stream);
 cudaError_t shard_phi_launch(const float *totals, int world, double *phi, cudaStream_t stream);
 
+// Small form (kpp_small.cu): one CTA, everything in shared memory.
+const void *small_lookup(int dt, int d);
+int small_threads();
+size_t small_smem(int64_t N, int d, int dt);
+cudaError_t small_launch(const void *fn, size_t smem, const Problem &p, cudaStream_t stream);
+
 // Runtime arguments of the persistent kernel.
 struct PersistArgs {
     int64_t cache_supers; // super-iterations of each warp's segment kept in smem

@@ -18,21 +18,19 @@ constexpr int kReadUnroll = 8;
 // never happens.
 __device__ uint32_t g_read_sink;
 
-// Each CTA reads one contiguous share of the buffer (as a seeding CTA reads
-// its row block), `reps` times in one launch, so that every CTA stays on its
-// SM from one sweep to the next -- what a small buffer left in the L2 slices
-// near that SM is then read from there, as in the persistent seeding form.
+// One launch sweeps the buffer `reps` times: thread i reads vectors i,
+// i + G, i + 2G, ... (G = all threads of the grid) in every sweep, so that
+// every CTA stays on its SM and reads the same addresses from one sweep to
+// the next -- what a small buffer left in the L2 slices near that SM is then
+// read from there, as the persistent seeding form re-reads its row block.
 __global__ void __launch_bounds__(kReadThreads) read_kernel(const uint4 *buf, int64_t n, int reps)
 {
-    const int64_t per = (n + gridDim.x - 1) / gridDim.x;
-    const int64_t b = (int64_t)blockIdx.x * per;
-    const int64_t e = (b + per) < n ? (b + per) : n;
-    const int64_t stride = blockDim.x;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     uint32_t acc = 0;
     for (int r = 0; r < reps; ++r) {
-        int64_t i = b + threadIdx.x;
+        int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
         // kReadUnroll independent 16-byte loads in flight per thread
-        for (; i + (kReadUnroll - 1) * stride < e; i += kReadUnroll * stride) {
+        for (; i + (kReadUnroll - 1) * stride < n; i += kReadUnroll * stride) {
             uint4 v[kReadUnroll];
 #pragma unroll
             for (int u = 0; u < kReadUnroll; ++u)
@@ -41,7 +39,7 @@ __global__ void __launch_bounds__(kReadThreads) read_kernel(const uint4 *buf, in
             for (int u = 0; u < kReadUnroll; ++u)
                 acc ^= v[u].x ^ v[u].y ^ v[u].z ^ v[u].w;
         }
-        for (; i < e; i += stride) {
+        for (; i < n; i += stride) {
             const uint4 v = ld_stream16(buf + i);
             acc ^= v.x ^ v.y ^ v.z ^ v.w;
         }

@@ -1,4 +1,4 @@
-// kpp_tune.cu -- the autotuner: chooses the form (persistent or streamed),
+// kpp_tune.cu -- the autotuner: chooses the form (small, persistent or streamed),
 // the lanes per row (points per warp iteration), the row block per CTA and
 // the shared-memory cache by timing the candidates on the caller's own data,
 // and records the winner for the automatic choice of later calls with the
@@ -49,13 +49,14 @@ kpp_options make_opts(int form, int lanes, int ctas_per_sm, int smem_cache, int 
     return o;
 }
 
-// The candidate grid: every built lanes-per-row specialisation of both forms;
-// for the persistent form with and without the shared-memory point cache and
+// The candidate grid: the small form (where the problem fits one SM), every
+// built lanes-per-row specialisation of the two other forms; for the persistent form with and without the shared-memory point cache and
 // three smallest row blocks per CTA, for the streamed form three grid sizes.
 std::vector<kpp_options> candidates()
 {
     static const int kLanes[] = {0, 1, 2, 4, 8, 16, 32};
     std::vector<kpp_options> c;
+    c.push_back(make_opts(KPP_FORM_SMALL, 0, 0, 0, 0));
     for (int lanes : kLanes) {
         for (int cache : {0, -1})
             for (int min_rows : {0, 512, 8192})
