@@ -292,7 +292,7 @@ def run_reference_other(args, world):
         ell, R = args.ell_mult * K, args.rounds
         n_s = int(min(N, max(4 * K, 3e9 / (ell * R * d))))
     x = datagen.gmm(n_s, d, wl.n_comp, wl.data_seed, wl.mean_box, wl.sigma, wl.weights,
-                    wl.outlier_frac)
+                    wl.outlier_frac, wl.outlier_center)
     C = x[:K].astype(np.float64)
     times = []
     for s_ in range(args.warmup + steps):
@@ -335,7 +335,7 @@ def run_reference(args, rank, world):
     # workloads too slowly for a bench run)
     x = datagen.workload_points(wl) if wl.N <= 2_000_000 else datagen.gmm(
         min(wl.N, 2_000_000), wl.d, wl.n_comp, wl.data_seed, wl.mean_box, wl.sigma, wl.weights,
-        wl.outlier_frac)
+        wl.outlier_frac, wl.outlier_center)
     N = x.shape[0]
     cores, model = cpu_info()
     # passes per step sized so that warm-up and timed steps take about two minutes

@@ -11,7 +11,9 @@ Gaussian mixture:
   mean_box]^d``; per-component isotropic sigma, fixed or uniform in
   ``sigma_range``; weights equal or Dirichlet(1); every point draws its
   component label i.i.d. (so point order is random).  numpy PCG64 generator,
-  machine independent.
+  machine independent.  A fraction of the rows can be replaced by
+  heavy-tailed 10 * Student-t(3) rows, centred at the origin or at their
+  component's mean.
 * ``gmm_torch(...)``: the same recipe drawn in chunks with a torch generator
   on a device, for the 10^7-10^8-point workloads that numpy draws too slowly.
 * ``WORKLOADS``: the named workloads, with their sizes.
@@ -42,6 +44,7 @@ class Workload:
     data_seed: int = 0
     draw_seed: int = 1
     outlier_frac: float = 0.0  # fraction replaced by 10 * Student-t(3) rows
+    outlier_center: str = "zero"  # "zero" | "component": where those rows are centred
 
 
 WORKLOADS = {
@@ -58,6 +61,11 @@ WORKLOADS = {
     "gmm-N2e7-d128-K2048-t3": Workload("gmm-N2e7-d128-K2048-t3", 20_000_000, 128,
                                        2048, 2048, 50.0, (0.5, 2.0), "dirichlet",
                                        outlier_frac=0.10),
+    # The other reading of the heavy-tailed rows: each centred at the mean of
+    # the component the row was drawn from, instead of at the origin.
+    "gmm-N2e7-d128-K2048-t3c": Workload("gmm-N2e7-d128-K2048-t3c", 20_000_000, 128,
+                                        2048, 2048, 50.0, (0.5, 2.0), "dirichlet",
+                                        outlier_frac=0.10, outlier_center="component"),
 }
 
 
@@ -75,8 +83,13 @@ def _mixture_params(rng: np.random.Generator, d: int, n_comp: int, mean_box: flo
 
 def gmm(N: int, d: int, n_comp: int, seed: int, mean_box: float = 50.0,
         sigma: tuple = (0.5, 2.0), weights: str = "dirichlet",
-        outlier_frac: float = 0.0) -> np.ndarray:
-    """Gaussian-mixture points, float32 [N, d] (numpy PCG64, seeded)."""
+        outlier_frac: float = 0.0, outlier_center: str = "zero") -> np.ndarray:
+    """Gaussian-mixture points, float32 [N, d] (numpy PCG64, seeded).
+
+    ``outlier_frac`` of the rows, chosen without replacement, are replaced by
+    10 * Student-t(3) draws, centred at the origin (``outlier_center`` "zero")
+    or at the mean of the row's component ("component").
+    """
     rng = np.random.default_rng(seed)
     means, sig, w = _mixture_params(rng, d, n_comp, mean_box, sigma, weights)
     labels = rng.choice(n_comp, size=N, p=w)
@@ -90,13 +103,18 @@ def gmm(N: int, d: int, n_comp: int, seed: int, mean_box: float = 50.0,
     if outlier_frac > 0.0:
         n_out = int(round(outlier_frac * N))
         rows = rng.choice(N, size=n_out, replace=False)
-        x[rows] = (10.0 * rng.standard_t(3.0, size=(n_out, d))).astype(np.float32)
+        t = 10.0 * rng.standard_t(3.0, size=(n_out, d))
+        if outlier_center == "component":
+            t = t + means[labels[rows]]
+        elif outlier_center != "zero":
+            raise ValueError(f"unknown outlier centre {outlier_center!r}")
+        x[rows] = t.astype(np.float32)
     return x
 
 
 def gmm_torch(N: int, d: int, n_comp: int, seed: int, device, mean_box: float = 50.0,
               sigma: tuple = (0.5, 2.0), weights: str = "dirichlet",
-              outlier_frac: float = 0.0):
+              outlier_frac: float = 0.0, outlier_center: str = "zero"):
     """The ``gmm`` recipe drawn with a torch generator on ``device`` (float32 [N, d]).
 
     Mixture parameters come from numpy (seeded); the per-point labels, normals
@@ -111,13 +129,19 @@ def gmm_torch(N: int, d: int, n_comp: int, seed: int, device, mean_box: float = 
     means_t = torch.as_tensor(means, dtype=torch.float32, device=device)
     sig_t = torch.as_tensor(sig, dtype=torch.float32, device=device)
     w_t = torch.as_tensor(w, dtype=torch.float64, device=device)
+    if outlier_center not in ("zero", "component"):
+        raise ValueError(f"unknown outlier centre {outlier_center!r}")
     x = torch.empty((N, d), dtype=torch.float32, device=device)
+    keep_labels = outlier_frac > 0.0 and outlier_center == "component"
+    labels = torch.empty(N, dtype=torch.int64, device=device) if keep_labels else None
     chunk = max(1, (1 << 26) // d)
     for s in range(0, N, chunk):
         e = min(N, s + chunk)
         lab = torch.multinomial(w_t, e - s, replacement=True, generator=g)
         z = torch.randn((e - s, d), generator=g, device=device, dtype=torch.float32)
         x[s:e] = means_t[lab] + sig_t[lab, None] * z
+        if keep_labels:
+            labels[s:e] = lab
     if outlier_frac > 0.0:
         n_out = int(round(outlier_frac * N))
         rows = torch.randperm(N, generator=g, device=device)[:n_out]
@@ -126,7 +150,10 @@ def gmm_torch(N: int, d: int, n_comp: int, seed: int, device, mean_box: float = 
             e = min(n_out, s + chunk)
             z = torch.randn((e - s, d), generator=g, device=device)
             c = torch.randn((e - s, d, 3), generator=g, device=device).square().sum(-1)
-            x[rows[s:e]] = 10.0 * z / torch.sqrt(c / 3.0)
+            t = 10.0 * z / torch.sqrt(c / 3.0)
+            if keep_labels:
+                t = t + means_t[labels[rows[s:e]]]
+            x[rows[s:e]] = t
     return x
 
 
@@ -134,9 +161,9 @@ def workload_points(wl: Workload, device=None):
     """Points of a named workload: numpy (device None) or a torch tensor."""
     if device is None:
         return gmm(wl.N, wl.d, wl.n_comp, wl.data_seed, wl.mean_box, wl.sigma,
-                   wl.weights, wl.outlier_frac)
+                   wl.weights, wl.outlier_frac, wl.outlier_center)
     return gmm_torch(wl.N, wl.d, wl.n_comp, wl.data_seed, device, wl.mean_box,
-                     wl.sigma, wl.weights, wl.outlier_frac)
+                     wl.sigma, wl.weights, wl.outlier_frac, wl.outlier_center)
 
 
 @dataclass(frozen=True)

@@ -16,6 +16,8 @@ def test_named_workloads():
     assert w["gmm-N1e7-d64-K1024"].K == 1024 and w["gmm-N1e7-d64-K1024"].n_comp == 1024
     big = w["gmm-N2e7-d128-K2048-t3"]
     assert (big.N, big.d, big.K, big.outlier_frac) == (20_000_000, 128, 2048, 0.10)
+    alt = datagen.WORKLOADS["gmm-N2e7-d128-K2048-t3c"]
+    assert (alt.N, alt.d, alt.K, alt.outlier_center) == (20_000_000, 128, 2048, "component")
     for name, wl in w.items():
         assert wl.name == name and wl.K <= wl.N and wl.draw_seed == 1
 
@@ -100,3 +102,32 @@ def test_torch_form_of_the_recipe_on_cpu():
             np.testing.assert_allclose(x[lab == k].mean(0), means[k], atol=0.2)
     o = datagen.gmm_torch(20_000, 4, 3, 7, "cpu", outlier_frac=0.1)
     assert (o != a).any(dim=1).sum().item() == 2000
+
+
+def test_heavy_tailed_rows_centred_at_their_component():
+    x = datagen.gmm(20_000, 4, 3, seed=1, outlier_frac=0.10, outlier_center="component")
+    y = datagen.gmm(20_000, 4, 3, seed=1, outlier_frac=0.10)
+    z = datagen.gmm(20_000, 4, 3, seed=1)
+    changed = np.any(x != z, axis=1)
+    assert changed.sum() == 2000 and np.array_equal(changed, np.any(y != z, axis=1))
+    # the same t draws, shifted by the row's component mean: the shift is one
+    # of the three means for every replaced row
+    rng = np.random.default_rng(1)
+    means, _, _ = datagen._mixture_params(rng, 4, 3, 50.0, (0.5, 2.0), "dirichlet")
+    shift = (x[changed].astype(np.float64) - y[changed].astype(np.float64))
+    dist = np.abs(shift[:, None, :] - means[None]).max(-1).min(1)
+    assert np.all(dist < 1e-3)
+    with pytest.raises(ValueError):
+        datagen.gmm(100, 2, 2, seed=0, outlier_frac=0.1, outlier_center="nowhere")
+
+
+def test_torch_form_centres_outliers_at_their_component():
+    torch = pytest.importorskip("torch")
+    a = datagen.gmm_torch(20_000, 4, 3, 7, "cpu", outlier_frac=0.1)
+    b = datagen.gmm_torch(20_000, 4, 3, 7, "cpu", outlier_frac=0.1, outlier_center="component")
+    rng = np.random.default_rng(7)
+    means, _, _ = datagen._mixture_params(rng, 4, 3, 50.0, (0.5, 2.0), "dirichlet")
+    changed = (a != b).any(dim=1).numpy()
+    assert 1_500 < changed.sum() <= 2_000  # rows whose shift is 0 in float32 stay equal
+    shift = (b.numpy()[changed] - a.numpy()[changed]).astype(np.float64)
+    assert np.all(np.abs(shift[:, None, :] - means[None]).max(-1).min(1) < 1e-3)
