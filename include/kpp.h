@@ -36,6 +36,13 @@
  * aligned).  A workspace must not be shared by calls in flight at the same
  * time.
  *
+ * Debug build: compiled with KPP_DEBUG=1, the kernels check the index of
+ * every shared- and global-memory access on their hot paths before making
+ * it; an index outside its buffer skips the access and records
+ * KPP_ERR_BOUNDS (with a site number) in the device status word, so a
+ * faulty index shows up as a status, never as a memory fault.  The release
+ * build compiles the checks away.
+ *
  * Asynchrony and errors: compute entry points enqueue work on `stream` and
  * return at once.  Argument errors are returned synchronously and nothing is
  * enqueued.  Errors found on the device (degenerate data, a barrier
@@ -70,7 +77,9 @@ typedef enum {
     KPP_ERR_DEGENERATE = 5,  /* sum D^2 = 0 before K seeds (device status) */
     KPP_ERR_WORKSPACE = 6,   /* workspace NULL, misaligned or too small */
     KPP_ERR_UNSUPPORTED = 7, /* option combination not built */
-    KPP_ERR_CAPACITY = 8     /* k-means||: more candidates than the caller's room */
+    KPP_ERR_CAPACITY = 8,    /* k-means||: more candidates than the caller's room */
+    KPP_ERR_BOUNDS = 9       /* debug build only (KPP_DEBUG): a kernel computed an index
+                                outside its buffer; the access was skipped (device status) */
 } kpp_status;
 
 /* Storage type of the points; distances are always accumulated in FP32. */

@@ -28,7 +28,7 @@ from . import build as _build
 F32, BF16, FP8_E4M3 = 0, 1, 2
 FORM_AUTO, FORM_STREAMED, FORM_PERSISTENT, FORM_RECOMPUTE, FORM_SMALL = 0, 1, 2, 3, 4
 (OK, ERR_INVALID_ARG, ERR_CUDA, ERR_LAUNCH, ERR_TIMEOUT, ERR_DEGENERATE,
- ERR_WORKSPACE, ERR_UNSUPPORTED, ERR_CAPACITY) = range(9)
+ ERR_WORKSPACE, ERR_UNSUPPORTED, ERR_CAPACITY, ERR_BOUNDS) = range(10)
 
 _DTYPE_NAMES = {"f32": F32, "fp32": F32, "float32": F32, "bf16": BF16, "bfloat16": BF16,
                 "fp8": FP8_E4M3, "e4m3": FP8_E4M3, "fp8_e4m3": FP8_E4M3}
@@ -90,8 +90,14 @@ class Shard(ctypes.Structure):
                 ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_size_t)]
 
 
+def debug_build() -> bool:
+    """True when the environment asks for the KPP_DEBUG build of the library
+    (KPP_DEBUG=1): index checks in the kernels, reported as KPP_ERR_BOUNDS."""
+    return os.environ.get("KPP_DEBUG", "0") not in ("", "0")
+
+
 def library_path() -> str:
-    return _build.LIB
+    return _build.lib_path(debug_build())
 
 
 def load_library(build_if_stale: bool = True):
@@ -100,7 +106,9 @@ def load_library(build_if_stale: bool = True):
     with _lock:
         if _lib is not None:
             return _lib
-        path = _build.build() if build_if_stale else _build.LIB
+        if build_if_stale:
+            _build.build()
+        path = library_path()
         if not os.path.exists(path):
             raise ImportError(f"libkpp.so not built at {path}")
         lib = ctypes.CDLL(path)

@@ -1,7 +1,9 @@
 """Build libkpp.so in-tree with nvcc for sm_103a (GB300).
 
 Every ``csrc/*.cu`` is compiled to an object in parallel and linked into
-``paper_1908_02136_gb300/_build/libkpp.so``.  Rebuilds only when a source or
+``paper_1908_02136_gb300/_build/libkpp.so``; the debug build (``KPP_DEBUG=1``:
+index checks before the hot kernels' memory accesses, reported as a device
+status) goes to ``_build_debug/libkpp.so``.  Rebuilds only when a source or
 header is newer than the library.  No cmake, no torch extension machinery.
 """
 from __future__ import annotations
@@ -19,6 +21,8 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libkpp.so")
+BUILD_DEBUG = os.path.join(PKG, "_build_debug")
+LIB_DEBUG = os.path.join(BUILD_DEBUG, "libkpp.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -41,23 +45,51 @@ def _inputs():
             + glob.glob(os.path.join(INCLUDE, "*.h")) + [os.path.abspath(__file__)])
 
 
-def stale() -> bool:
-    if not os.path.exists(LIB):
+def lib_path(debug: bool = False) -> str:
+    return LIB_DEBUG if debug else LIB
+
+
+def stale(debug: bool = False) -> bool:
+    lib = lib_path(debug)
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return any(os.path.getmtime(f) > t for f in _inputs())
 
 
-def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) -> str:
-    """Compile and link libkpp.so; returns its path."""
-    if not force and not stale():
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
-    extra = ["-Xptxas", "-v"] if ptxas_info else []
+def _compile_jobs(debug: bool, extra):
+    out = BUILD_DEBUG if debug else BUILD
+    flags = _flags(list(extra) + (["-DKPP_DEBUG=1"] if debug else []))
+    return [(src, os.path.join(out, os.path.basename(src)[:-3] + ".o"), flags)
+            for src in sources()]
 
-    def compile_one(src):
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
-        cmd = [nvcc(), "-c", src, "-o", obj, *_flags(extra)]
+
+def _link(objs, lib):
+    tmp = lib + f".tmp{os.getpid()}"
+    cmd = [nvcc(), "-shared", *ARCH, "-o", tmp, *objs, "-Xcompiler", "-fPIC"]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"nvcc link failed:\n{r.stdout}\n{r.stderr}")
+    os.replace(tmp, lib)
+
+
+def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False,
+          debug: bool = True) -> str:
+    """Compile and link libkpp.so (and, with ``debug``, its KPP_DEBUG build,
+    compiled in the same parallel pool); returns the release library's path."""
+    variants = [False] + ([True] if debug else [])
+    todo = [v for v in variants if force or stale(v)]
+    if not todo:
+        return LIB
+    extra = ["-Xptxas", "-v"] if ptxas_info else []
+    jobs = []
+    for v in todo:
+        os.makedirs(BUILD_DEBUG if v else BUILD, exist_ok=True)
+        jobs += [(v, *j) for j in _compile_jobs(v, extra)]
+
+    def compile_one(job):
+        _, src, obj, flags = job
+        cmd = [nvcc(), "-c", src, "-o", obj, *flags]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed on {src}:\n{r.stdout}\n{r.stderr}")
@@ -65,15 +97,10 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
             sys.stderr.write(r.stdout + r.stderr)
         return obj
 
-    srcs = sources()
-    with ThreadPoolExecutor(max_workers=min(len(srcs), os.cpu_count() or 4)) as ex:
-        objs = list(ex.map(compile_one, srcs))
-    tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [nvcc(), "-shared", *ARCH, "-o", tmp, *objs, "-Xcompiler", "-fPIC"]
-    r = subprocess.run(cmd, capture_output=True, text=True)
-    if r.returncode != 0:
-        raise RuntimeError(f"nvcc link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
+    with ThreadPoolExecutor(max_workers=min(len(jobs), os.cpu_count() or 4)) as ex:
+        objs = list(ex.map(compile_one, jobs))
+    for v in todo:
+        _link([o for j, o in zip(jobs, objs) if j[0] == v], lib_path(v))
     return LIB
 
 

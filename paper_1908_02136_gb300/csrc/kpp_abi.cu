@@ -406,6 +406,8 @@ const char *kpp_status_string(kpp_status s)
         return "unsupported option combination";
     case KPP_ERR_CAPACITY:
         return "more k-means|| candidates than the room given";
+    case KPP_ERR_BOUNDS:
+        return "debug build: a kernel index was out of bounds (access skipped)";
     }
     return "unknown status";
 }

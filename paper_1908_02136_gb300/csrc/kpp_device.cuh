@@ -23,8 +23,32 @@ struct Control {
     uint32_t ticket;         // streamed form: CTAs finished with the current pass
     unsigned long long mail; // persistent form: (drawn index << 32) | (pass + 1)
     uint32_t timeout_where;  // persistent form: pass whose wait gave up
-    uint32_t pad_[59];
+    uint32_t bounds_site;    // debug build: site of the first index out of bounds
+    uint32_t pad_[58];
 };
+
+// ---------------------------------------------------------------------------
+// Debug build (KPP_DEBUG=1): index checks before the memory accesses of the
+// hot kernels.  A check that fails records KPP_ERR_BOUNDS and its site in the
+// status block (the first one wins) and tells the caller to skip the access;
+// the release build compiles every check to `true`.
+// ---------------------------------------------------------------------------
+#ifndef KPP_DEBUG
+#define KPP_DEBUG 0
+#endif
+
+__device__ __forceinline__ bool kpp_check(Control *ctl, bool ok, uint32_t site)
+{
+#if KPP_DEBUG
+    if (!ok && ctl && atomicCAS(&ctl->status, KPP_OK, KPP_ERR_BOUNDS) == KPP_OK)
+        atomicExch(&ctl->bounds_site, site);
+    return ok;
+#else
+    (void)ctl;
+    (void)site;
+    return true;
+#endif
+}
 
 // One tagged block sum per 32-byte slot, so the slots polled by every CTA
 // sit in different sectors.

@@ -168,6 +168,7 @@ struct PassIO {
     float *d2s;            // D2_SMEM: shared memory, indexed by row - r0
     float2 *segs;          // segment sums of this CTA, one per warp (global or smem)
     uint64_t policy;       // L2 cache policy of global point loads (0: none)
+    Control *ctl;          // status block (debug build: index checks report here)
 };
 
 __device__ __forceinline__ uint4 ld_global_hint(const void *ptr, uint64_t policy)
@@ -220,6 +221,13 @@ __device__ __forceinline__ void sts16(void *p, uint4 v)
 __device__ __forceinline__ uint4 load_vec(const PassIO &io, const char *cslot, int64_t rb,
                                           int64_t row, int byte_in_row, int RB)
 {
+    // the 16 bytes read lie within this CTA's rows (a narrow-row vector
+    // covers several whole rows)
+    if (!kpp_check(io.ctl,
+                   row * RB + byte_in_row >= io.r0 * RB &&
+                       row * RB + byte_in_row + 16 <= io.r1 * RB,
+                   101))
+        return make_uint4(0, 0, 0, 0);
     if (cslot)
         return lds16(cslot + (row - rb) * RB + byte_in_row);
     const char *g = io.gpts + row * RB + byte_in_row;
@@ -234,6 +242,8 @@ __device__ __forceinline__ float prefetch_d2(const PassIO &io, int64_t row, bool
 {
     if (MODE != D2_INPLACE || io.first || !in_range)
         return 0.f;
+    if (!kpp_check(io.ctl, row >= io.r0 && row < io.r1, 102))
+        return 0.f;
     return __ldcg(io.d2 + row);
 }
 
@@ -242,6 +252,8 @@ __device__ __forceinline__ float prefetch_d2(const PassIO &io, int64_t row, bool
 template <int MODE>
 __device__ __forceinline__ float update_d2(const PassIO &io, int64_t row, float v, float pre)
 {
+    if (!kpp_check(io.ctl, row >= io.r0 && row < io.r1, 103))
+        return 0.f;
     float *slot = (MODE == D2_INPLACE) ? io.d2 + row : io.d2s + (row - io.r0);
     if (io.first) {
         *slot = v;
@@ -303,7 +315,9 @@ __device__ __forceinline__ Pair pass_rows(const PassIO &io, const CentreRegs<DT,
                 const int64_t own_row = rb + (int64_t)l * (32 / G::L) + g;
                 pre = prefetch_d2<MODE>(io, own_row, own_row < seg_last);
             }
-            if (rb + G::SW <= seg_last) {
+            if (rb + G::SW <= seg_last &&
+                kpp_check(io.ctl,
+                          row0 >= io.r0 && row0 + (int64_t)(G::JB - 1) * (32 / G::L) < io.r1, 104)) {
                 // whole super-iteration in range: no bounds checks, one base
                 // address and immediate offsets
                 if (from) {
@@ -325,6 +339,16 @@ __device__ __forceinline__ Pair pass_rows(const PassIO &io, const CentreRegs<DT,
 #pragma unroll
                 for (int q = 0; q < G::JB; ++q)
                     sc[q] = (DT == KPP_FP8_E4M3) ? __ldg(io.scales + row0 + q * (32 / G::L)) : 1.0f;
+                return;
+            }
+            if (rb + G::SW <= seg_last) { // only after a failed debug check
+#pragma unroll
+                for (int q = 0; q < G::JB; ++q) {
+                    sc[q] = 1.0f;
+#pragma unroll
+                    for (int v = 0; v < G::VPL; ++v)
+                        x[q][v] = make_uint4(0, 0, 0, 0);
+                }
                 return;
             }
 #pragma unroll
@@ -432,7 +456,7 @@ __device__ __forceinline__ Pair pass_rows(const PassIO &io, const CentreRegs<DT,
 #pragma unroll
                 for (int r = 0; r < G::RPV; ++r) {
                     const int64_t row = own_row + r;
-                    const bool ok = row < seg_last;
+                    const bool ok = row < seg_last && kpp_check(io.ctl, row >= io.r0 && row < io.r1, 105);
                     sc[r] = (DT == KPP_FP8_E4M3 && ok) ? __ldg(io.scales + row) : 1.0f;
 #pragma unroll
                     for (int k = 0; k < D; ++k)

@@ -81,6 +81,13 @@ __device__ __forceinline__ void seed_blocks(const Problem &p, const PersistArgs 
     const uint64_t policy =
         a.l2_hint == 1 ? policy_evict_last() : (a.l2_hint == 2 ? policy_evict_first() : 0ull);
 
+    // the plan's limits: this block exists, the level-1 stage and the chunk
+    // sums hold what the draw will put there (every CTA sees the same values)
+    if (!kpp_check(p.ctl,
+                   b >= 0 && b < p.nblocks && p.nblocks <= kMaxBlocks && r0 < r1 &&
+                       (!chunk_path || nchunks <= kMaxChunks),
+                   201))
+        return;
     int64_t ci = first_seed(p);
     if (ci < 0 || ci >= p.N) {
         if (b == 0 && threadIdx.x == 0)
@@ -101,6 +108,7 @@ __device__ __forceinline__ void seed_blocks(const Problem &p, const PersistArgs 
         cr.load(p.points, p.scales, ci);
 
         PassIO io{};
+        io.ctl = p.ctl;
         io.r0 = r0;
         io.r1 = r1;
         io.first = (m == 0);
@@ -183,8 +191,9 @@ __device__ __forceinline__ void seed_blocks(const Problem &p, const PersistArgs 
                     const int64_t rb = r0 + 32ll * c;
                     const int n = (int)((r1 - rb) < 32 ? (r1 - rb) : 32);
                     Pair cs{};
-                    for (int k = 0; k < n; ++k)
-                        cs.add(d2s[rb - r0 + k]);
+                    if (kpp_check(p.ctl, rb - r0 + n <= p.chunk, 202))
+                        for (int k = 0; k < n; ++k)
+                            cs.add(d2s[rb - r0 + k]);
                     chunk_sums[c] = make_float2(cs.hi, cs.lo);
                 }
             }
@@ -222,7 +231,11 @@ __device__ __forceinline__ void seed_blocks(const Problem &p, const PersistArgs 
 
         if (owner == b) {
             // the point within this block; then publish the index
-            auto d2_at = [&](int64_t row) { return MODE == D2_SMEM ? d2s[row - r0] : p.d2[row]; };
+            auto d2_at = [&](int64_t row) {
+                if (!kpp_check(p.ctl, row >= r0 && row < r1, 203))
+                    return 0.f;
+                return MODE == D2_SMEM ? d2s[row - r0] : p.d2[row];
+            };
             int64_t pick = -1;
             if (chunk_path) {
                 // from the 32-row chunk sums made during the wait, by warp 0
@@ -242,7 +255,10 @@ __device__ __forceinline__ void seed_blocks(const Problem &p, const PersistArgs 
                     }
                     const int64_t rb = r0 + 32ll * c;
                     const int n = (int)((r1 - rb) < 32 ? (r1 - rb) : 32);
-                    const float v = lane < n ? d2s[rb - r0 + lane] : 0.f;
+                    const float v =
+                        (lane < n && kpp_check(p.ctl, rb - r0 + lane < p.chunk && c < nchunks, 204))
+                            ? d2s[rb - r0 + lane]
+                            : 0.f;
                     const Find32 f = warp_find32(n, Pair{v, 0.f}, before, t);
                     pick = rb + (f.index >= 0 ? f.index : 0);
                 }
@@ -306,6 +322,7 @@ __device__ __forceinline__ void seed_blocks(const Problem &p, const PersistArgs 
                 }
             }
             if (threadIdx.x == 0) {
+                kpp_check(p.ctl, pick >= r0 && pick < r1, 205);
                 p.idx[next] = pick;
                 st_relaxed_u64(p.mail,
                                ((unsigned long long)pick << 32) | (unsigned long long)(uint32_t)next);

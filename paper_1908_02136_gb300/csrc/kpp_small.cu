@@ -102,6 +102,8 @@ __global__ void __launch_bounds__(kSmallThreads, 1) small_kernel(Problem p)
     const int P = (N + kSmallThreads - 1) / kSmallThreads;
     const int r0 = tid * P < N ? tid * P : N;
     const int r1 = r0 + P < N ? r0 + P : N;
+    if (!kpp_check(p.ctl, r0 >= 0 && r1 <= N && r0 <= r1, 401))
+        return;
 
     int64_t ci = first_seed(p);
     if (ci < 0 || ci >= N) { // a forced first index out of range (same on every thread)
@@ -129,6 +131,8 @@ __global__ void __launch_bounds__(kSmallThreads, 1) small_kernel(Problem p)
         // the centre, decoded as the other forms decode it (FP8: c = s * q
         // as an exact pair), then the distance, min-update and pair sum of
         // this thread's rows
+        if (!kpp_check(p.ctl, ci >= 0 && ci < N, 403))
+            ci = 0;
         const float cs = (DT == KPP_FP8_E4M3) ? S[ci] : 1.f;
         const float *crow = X + ci * d;
         Pair acc{};
@@ -263,6 +267,8 @@ __global__ void __launch_bounds__(kSmallThreads, 1) small_kernel(Problem p)
                     }
                     if (pick < 0)
                         pick = lastpos >= 0 ? lastpos : r0;
+                    if (!kpp_check(p.ctl, pick >= 0 && pick < N, 402))
+                        pick = 0;
                     sh.pick = pick;
                     p.idx[next] = pick;
                 }

@@ -71,6 +71,8 @@ __device__ __forceinline__ void finish_pass(const Problem &p, int m, const Pair 
     if (!is_last)
         return;
     __threadfence();
+    if (!kpp_check(p.ctl, p.nblocks <= kStage && (int)blockIdx.x < p.nblocks, 301))
+        return;
     for (int k = threadIdx.x; k < p.nblocks; k += blockDim.x)
         stage_pairs[k] = __ldcg(p.block_sums + k);
     __syncthreads();
@@ -155,8 +157,13 @@ __device__ __forceinline__ void finish_pass(const Problem &p, int m, const Pair 
     int64_t first, last;
     segment_rows(row0, rows_blk, p.sw, p.nseg, (int)seg_sh, &first, &last);
     const int64_t pick = warp_rows_find(
-        first, last, [&](int64_t row) { return __ldcg(p.d2 + row); }, before_sh, th_sh);
+        first, last,
+        [&](int64_t row) {
+            return kpp_check(p.ctl, row >= 0 && row < p.N, 302) ? __ldcg(p.d2 + row) : 0.f;
+        },
+        before_sh, th_sh);
     if (threadIdx.x == 0) {
+        kpp_check(p.ctl, blk < p.nblocks && pick >= row0 && pick < row0 + rows_blk, 303);
         p.idx[next] = pick;
         p.ctl->ticket = 0u; // ready for the next launch
     }
@@ -170,6 +177,7 @@ __global__ void __launch_bounds__(kStreamThreads)
     if (ci < 0)
         return;
     PassIO io{};
+    io.ctl = p.ctl;
     io.r0 = (int64_t)blockIdx.x * p.chunk;
     io.r1 = (io.r0 + p.chunk) < p.N ? (io.r0 + p.chunk) : p.N;
     io.gpts = reinterpret_cast<const char *>(p.points);
@@ -202,6 +210,7 @@ __global__ void __launch_bounds__(kStreamThreads)
     if (ci < 0)
         return;
     PassIO io{};
+    io.ctl = p.ctl;
     io.r0 = (int64_t)blockIdx.x * p.chunk;
     io.r1 = (io.r0 + p.chunk) < p.N ? (io.r0 + p.chunk) : p.N;
     io.gpts = reinterpret_cast<const char *>(p.points);
@@ -237,6 +246,8 @@ __device__ __forceinline__ void shard_put_row(const Problem &p, int64_t r, int64
                                               long long *xchg, int eb)
 {
     const int64_t rb = (int64_t)p.d * eb;
+    if (!kpp_check(p.ctl, r >= 0 && r < p.N, 603))
+        return;
     const unsigned char *src = reinterpret_cast<const unsigned char *>(p.points) + r * rb;
     unsigned char *dst = reinterpret_cast<unsigned char *>(xchg + 2);
     for (int64_t k = threadIdx.x; k < rb; k += blockDim.x)
@@ -351,9 +362,13 @@ __global__ void __launch_bounds__(kStreamThreads)
         int64_t first, last;
         segment_rows(rb0, rows_blk, p.sw, p.nseg, (int)seg, &first, &last);
         const int64_t pick = warp_rows_find(
-            first, last, [&](int64_t row) { return __ldcg(p.d2 + row); }, before, th);
+            first, last,
+            [&](int64_t row) {
+                return kpp_check(p.ctl, row >= 0 && row < p.N, 601) ? __ldcg(p.d2 + row) : 0.f;
+            },
+            before, th);
         if (lane == 0)
-            pick_sh = pick;
+            pick_sh = kpp_check(p.ctl, blk < p.nblocks && pick >= 0 && pick < p.N, 602) ? pick : 0;
     }
     __syncthreads();
     shard_put_row(p, pick_sh, row0 + pick_sh, xchg, eb);

@@ -39,10 +39,11 @@ def test_header_declares_the_boundary():
         assert required in names
 
 
-def test_every_declared_symbol_is_exported(lib):
-    import paper_1908_02136_gb300 as kpp
+@pytest.mark.parametrize("debug", [False, True])
+def test_every_declared_symbol_is_exported(lib, debug):
+    from paper_1908_02136_gb300 import build
 
-    out = subprocess.run(["nm", "-D", "--defined-only", kpp.library_path()],
+    out = subprocess.run(["nm", "-D", "--defined-only", build.lib_path(debug)],
                          capture_output=True, text=True, check=True).stdout
     exported = set(re.findall(r"\bT\s+(\w+)", out))
     for name in declared_entry_points():
@@ -57,7 +58,7 @@ def test_host_only_entry_points(lib):
     import paper_1908_02136_gb300 as kpp
 
     assert kpp.kpp_version() >= 100
-    for code in range(9):
+    for code in range(10):
         s = kpp.kpp_status_string(code)
         assert isinstance(s, str) and s and s != "unknown status"
     assert kpp.kpp_status_string(99) == "unknown status"
