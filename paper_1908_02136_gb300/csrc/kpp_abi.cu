@@ -317,10 +317,9 @@ kpp_status run_persistent(const Plan &pl, const Problem &p, cudaStream_t stream)
                : KPP_ERR_LAUNCH;
 }
 
+// The small kernel clears its own status word: one launch per seeding.
 kpp_status run_small(const Plan &pl, const Problem &p, cudaStream_t stream)
 {
-    if (cudaMemsetAsync(p.ctl, 0, sizeof(Control), stream) != cudaSuccess)
-        return KPP_ERR_CUDA;
     return small_launch(pl.pfn, pl.psmem, p, stream) == cudaSuccess ? KPP_OK : KPP_ERR_LAUNCH;
 }
 

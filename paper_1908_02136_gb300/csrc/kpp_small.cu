@@ -54,6 +54,11 @@ __global__ void __launch_bounds__(kSmallThreads, 1) small_kernel(Problem p)
     const int d = D > 0 ? D : p.d;
     const int N = (int)p.N;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) { // the status block starts clean (no memset launch before this one)
+        p.ctl->status = KPP_OK;
+        p.ctl->bounds_site = 0;
+    }
+    __syncthreads();
     float *X = smem_f;                                  // [N x d] stored values (FP8: E4M3 value)
     float *S = X + (int64_t)N * d;                      // [N] FP8 row scales
     float *D2 = S + (DT == KPP_FP8_E4M3 ? N : 0);       // [N]

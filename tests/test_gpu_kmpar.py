@@ -23,6 +23,7 @@ import pytest
 import torch
 
 import oracle
+import parity
 import paper_1908_02136_gb300 as kpp
 from paper_1908_02136_gb300 import datagen
 
@@ -109,11 +110,11 @@ def test_float_regime_replayed_round_by_round(N, d, K, ell):
         assert np.max(np.abs(g["d2"][nz] - dist_g[nz]) / dist_g[nz]) <= 1e-5
         arg, best = _nearest(X, C)
         diff = lab != arg
-        bound = (2.0 ** -12 * np.linalg.norm(X, axis=1) * np.linalg.norm(C, axis=1).max()
+        bound = (parity.LABEL_BOUND * np.linalg.norm(X, axis=1) * np.linalg.norm(C, axis=1).max()
                  + 1e-30)
         assert np.all(dist_g[diff] - best[diff] <= bound[diff])
         events += int(diff.sum())
-        assert diff.sum() <= 0.05 * N
+        assert diff.sum() <= max(2, parity.LABEL_EVENT_FRAC * N)
         phi = float(g["phi"][0])
         assert phi == pytest.approx(g["d2"].astype(np.float64).sum(), rel=1e-12)
         assert np.array_equal(g["weights"], np.bincount(lab, minlength=cand.size))
@@ -232,9 +233,9 @@ def test_full_size_workload_sampled():
     nz = held > 0  # a sampled row may be a candidate itself
     assert np.all(d2[~nz] == 0)
     assert np.max(np.abs(d2[nz] - held[nz]) / held[nz]) <= 1e-5
-    bound = 2.0 ** -12 * np.linalg.norm(X, axis=1) * np.linalg.norm(C, axis=1).max()
+    bound = parity.LABEL_BOUND * np.linalg.norm(X, axis=1) * np.linalg.norm(C, axis=1).max()
     assert np.all(held - best <= bound)
-    assert np.mean(lab[rows] != arg) <= 0.05
+    assert np.mean(lab[rows] != arg) <= max(2 / len(rows), parity.LABEL_EVENT_FRAC)
     # the recluster, replayed on the candidates' own rows
     idx = r5["idx"].cpu().numpy()
     pos_of = {int(c): i for i, c in enumerate(c5)}
