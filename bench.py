@@ -6,23 +6,29 @@ HBM.  L2 is flushed (a 512 MiB buffer is written) between timed steps, and
 each step is timed with CUDA events on the launching stream.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
-                  [--dtype f32|bf16|fp8] [--impl kpp|reference]
+                  [--dtype f32|bf16|fp8] [--forms bf16,fp8|none]
+                  [--shard replicas|points] [--impl kpp|reference]
 
-Workloads: the seeding workloads (default gmm-N1e6-d32-K256), ``batch-512``
-(kpp_seed_batched over 512 uneven problems), ``lloyd-<seeding workload>``
-(one Lloyd iteration from that workload's k-means++ seeds; the assignment is
-also timed alone for its tensor roofline) and ``kmpar-<seeding workload>``
-(one whole k-means|| initialisation, ell = --ell-mult x K, --rounds rounds;
-its nearest-candidate search timed alone for the roofline).
+Workloads: the seeding workloads (default gmm-N2e7-d128-K2048-t3, the
+largest single-GPU one: 2e7 x 128, K = 2048; an FP32 run also times the same
+data stored as BF16 and FP8, --forms), ``batch-512`` (kpp_seed_batched over
+512 uneven problems), ``lloyd-<seeding workload>`` (one Lloyd iteration from
+that workload's k-means++ seeds; the assignment is also timed alone for its
+tensor roofline) and ``kmpar-<seeding workload>`` (one whole k-means||
+initialisation, ell = --ell-mult x K, --rounds rounds; its nearest-candidate
+search timed alone for the roofline).
 
-Under torchrun (N > 1), with no collective on the data path: for a single
-problem every rank seeds its own replica of the workload (its own Philox
-stream): weak scaling; for the 512-problem batch the problems are split
-between the ranks: strong scaling.  Timing is barrier-bracketed and the max
-over ranks is reported.
+Under torchrun (N > 1): for a single problem every rank seeds its own
+replica of the workload (its own Philox stream: weak scaling), or, with
+``--shard points``, the ranks split one problem by rows and exchange two
+small messages per pass over NCCL (strong scaling); for the 512-problem
+batch the problems are split between the ranks with no collective on the
+data path (strong scaling).  Timing is barrier-bracketed and the max over
+ranks is reported.
 
 ``--impl reference`` times the FP64 CPU oracle (the correctness reference,
-not a GPU code) on a bounded sample of the same workload on the host cores.
+not a GPU code; multi-threaded over the host cores for the seeding
+workloads) on a bounded sample of the same workload.
 """
 from __future__ import annotations
 
