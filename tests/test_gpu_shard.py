@@ -120,3 +120,40 @@ def test_sharded_argument_errors():
                               kpp._stream_handle(torch.device(DEV))) == kpp.ERR_INVALID_ARG
     assert kpp.kpp_shard_pick(s.desc, 3, s.totals.data_ptr(), s.exchange.data_ptr(),
                               kpp._stream_handle(torch.device(DEV))) == kpp.ERR_INVALID_ARG
+
+
+_NCCL_CHILD = r"""
+import os, sys, numpy as np, torch, torch.distributed as dist
+sys.path.insert(0, os.getcwd())
+import oracle
+import paper_1908_02136_gb300 as kpp
+from paper_1908_02136_gb300 import datagen, multi
+dist.init_process_group("nccl", rank=0, world_size=1, device_id=torch.device("cuda:0"))
+x = datagen.integer_points(30_011, 16, seed=3, n_comp=8)
+lo, hi = multi.shard_rows(len(x), 1)[0]
+s = kpp.PointShard(torch.from_numpy(x[lo:hi]).to("cuda:0"), lo, len(x), 24, 5, 0, 0, 1)
+multi.seed_sharded([s], multi.ProcessGroupComm(dist), 24)
+torch.cuda.synchronize()
+ref = oracle.seed(x, 24, 5, 0)
+assert s.status() == kpp.OK
+assert np.array_equal(s.idx.cpu().numpy(), ref["idx"])
+assert np.array_equal(s.d2.cpu().numpy().astype(np.float64), ref["d2"])
+assert float(s.phi.cpu()[0]) == ref["phi"]
+dist.destroy_process_group()
+print("nccl protocol ok")
+"""
+
+
+def test_protocol_over_nccl_on_one_rank():
+    """The exchanges as NCCL collectives through torch.distributed (a
+    one-rank group: the process-group path the multi-GPU run takes, on the
+    one GPU here), bit-identical to the oracle on integer data."""
+    import os
+    import subprocess
+    import sys
+
+    env = dict(os.environ, MASTER_ADDR="127.0.0.1", MASTER_PORT=str(29500 + os.getpid() % 1000))
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-c", _NCCL_CHILD], capture_output=True, text=True,
+                       cwd=root, env=env, timeout=600)
+    assert r.returncode == 0 and "nccl protocol ok" in r.stdout, r.stdout[-2000:] + r.stderr[-3000:]
