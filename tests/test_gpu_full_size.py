@@ -103,3 +103,62 @@ def test_full_size_sampled_parity(name, dtype, form):
             assert np.all(np.abs(before + P - t) <= 1e-9 * T), (m, j, idx[m])
             events += 1
     assert events <= 1
+
+
+def _sharded(stored, K, world):
+    """One point-sharded seeding of `stored` with `world` shards on this GPU
+    (each shard's rows in an allocation of its own); returns numpy idx, D^2
+    (all rows, in order) and phi."""
+    from paper_1908_02136_gb300 import multi
+
+    N = stored.shape[0]
+    shards = [kpp.PointShard(stored[lo:hi].clone(), lo, N, K, SEED, 0, r, world)
+              for r, (lo, hi) in enumerate(multi.shard_rows(N, world))]
+    multi.seed_sharded(shards, multi.InProcessComm(), K)
+    torch.cuda.synchronize()
+    assert all(s.status() == kpp.OK for s in shards)
+    idx = shards[0].idx.cpu().numpy()
+    for s in shards[1:]:
+        assert np.array_equal(s.idx.cpu().numpy(), idx)
+    d2 = np.concatenate([s.d2.cpu().numpy() for s in shards])
+    return idx, d2, float(shards[0].phi.cpu()[0])
+
+
+@pytest.mark.parametrize("name,world", [("gmm-N1e7-d64-K1024", 3), ("gmm-N2e7-d128-K2048-t3", 2)])
+def test_full_size_sharded_parity(name, world):
+    """The point-sharded form at the full sizes, its shards on this GPU: the
+    same sampled checks as the single-GPU forms above."""
+    wl = datagen.WORKLOADS[name]
+    N, d, K = wl.N, wl.d, wl.K
+    x = datagen.workload_points(wl, DEV)
+    idx, d2, phi = _sharded(x, K, world)
+    assert np.all((idx >= 0) & (idx < N)) and len(np.unique(idx)) == K
+    assert np.all(d2[idx] == 0.0) and np.all(d2 >= 0.0)
+    s64 = d2.astype(np.float64).sum()
+    assert abs(phi - s64) <= 1e-9 * s64
+    assert idx[0] == min(int(oracle.uniform(SEED, 0, 0) * N), N - 1)
+    rng = np.random.default_rng(11)
+    rows = np.sort(rng.choice(N, 2000, replace=False))
+    xs = _decode(x, None, "f32", rows)
+    cs = _decode(x, None, "f32", idx)
+    best = np.full(rows.size, np.inf)
+    for k0 in range(0, K, 128):
+        diff = xs[:, None, :] - cs[None, k0:k0 + 128, :]
+        best = np.minimum(best, np.einsum("ijk,ijk->ij", diff, diff).min(axis=1))
+    got = d2[rows].astype(np.float64)
+    zero = best == 0.0
+    assert np.all(got[zero] == 0.0)
+    assert (np.abs(got[~zero] - best[~zero]) / best[~zero]).max() <= 1e-5
+    events = 0
+    for m in (1, K // 2, K - 1):
+        i_m, d2m, _ = _sharded(x, m, world)
+        assert np.array_equal(i_m, idx[:m])  # same trajectory
+        d2m = d2m.astype(np.float64)
+        j, t, T = oracle.pick(d2m, oracle.uniform(SEED, 0, m))
+        if j != idx[m]:
+            lo, hi = sorted((j, int(idx[m])))
+            P = np.cumsum(d2m[lo:hi])
+            before = d2m[:lo].sum()
+            assert np.all(np.abs(before + P - t) <= 1e-9 * T), (m, j, idx[m])
+            events += 1
+    assert events <= 1
