@@ -82,6 +82,8 @@ def parse():
                     help="skip the live pure-read bandwidth measurement")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-parity-sample", action="store_true",
+                    help="skip the sampled D^2 check of the timed seeding")
     ap.add_argument("--no-phi", action="store_true")
     ap.add_argument("--no-sequential", action="store_true")
     ap.add_argument("--no-tune", action="store_true",
@@ -1002,6 +1004,8 @@ def run_seeding(args, rank, world, local, dev, pg, barrier):
     if dtype != "f32" and not args.no_phi:
         precision = phi_gate(dtype, main_r)
         precision["quantize_ms"] = q_ms
+    parity = None if args.no_parity_sample else sampled_parity(main_r, pts, scales, dtype, N, K,
+                                                               seed, stream_id)
 
     # precision forms of the same data beside the FP32 headline
     forms_block = None
@@ -1079,7 +1083,7 @@ def run_seeding(args, rank, world, local, dev, pg, barrier):
                        "step_ms_max": max(main_r["step_ms"])},
             "clocks": main_r["clocks"], "e2e": e2e,
             "gpu_launches": plan["launches"] * args.steps,
-            "precision": precision, "forms": forms_block,
+            "precision": precision, "forms": forms_block, "parity_sample": parity,
             "read_peaks": peaks_live,
             "roofline": roofline, "cpu_baseline": cpu_baseline,
         }), flush=True)
@@ -1162,6 +1166,47 @@ def run_sharded_seeding(args, rank, world, local, dev, pg, barrier):
                          "algorithmic_bytes_per_pass_rank0": per_pass},
             "cpu_baseline": None,
         }), flush=True)
+
+
+def sampled_parity(r, pts, scales, dtype, N, K, seed, stream_id, n_rows: int = 2000):
+    """Checks of the timed seeding's own output that any size allows (plain
+    FP64 numpy on a sample, not the oracle): the indices are distinct and in
+    range, D^2 is 0 at every chosen point, and the D^2 of `n_rows` sampled
+    rows equals, within 1e-5 relative, the FP64 minimum of the squared
+    distances from the stored values to all K chosen centres."""
+    import numpy as np
+    import torch
+
+    idx = r["idx"].cpu().numpy()
+    d2 = r["d2"]
+    rng = np.random.default_rng(12345)
+    rows = np.sort(rng.choice(N, min(N, n_rows), replace=False))
+
+    def decode(sel):
+        t = torch.as_tensor(sel, device=pts.device)
+        if dtype == "f32":
+            return pts[t].double().cpu().numpy()
+        if dtype == "bf16":
+            return pts[t].view(torch.bfloat16).double().cpu().numpy()
+        q = pts[t].view(torch.float8_e4m3fn).double()
+        return (q * scales[t].double()[:, None]).cpu().numpy()
+
+    xs, cs = decode(rows), decode(idx)
+    best = np.full(rows.size, np.inf)
+    for k0 in range(0, K, 128):
+        diff = xs[:, None, :] - cs[None, k0:k0 + 128, :]
+        best = np.minimum(best, np.einsum("ijk,ijk->ij", diff, diff).min(axis=1))
+    got = d2[torch.as_tensor(rows, device=d2.device)].double().cpu().numpy()
+    zero = best == 0.0
+    rel = np.abs(got[~zero] - best[~zero]) / best[~zero]
+    ok_zero = bool(np.all(got[zero] == 0.0))
+    chosen_zero = bool(float(d2[r["idx"]].abs().max()) == 0.0)
+    return {"rows": int(rows.size), "max_rel_d2_err": float(rel.max()) if rel.size else 0.0,
+            "d2_tolerance": 1e-5, "zero_where_expected": ok_zero,
+            "chosen_points_zero": chosen_zero,
+            "distinct_in_range": bool(len(set(idx.tolist())) == K and (idx >= 0).all()
+                                      and (idx < N).all()),
+            "ok": bool((rel.max() if rel.size else 0.0) <= 1e-5 and ok_zero and chosen_zero)}
 
 
 def oracle_baseline(stored, scales, K, seed, stream_id, budget_s: float = 15.0):

@@ -314,13 +314,21 @@ KPP_API kpp_status kpp_seed_batched(const kpp_problem *problems, int32_t n, kpp_
  * Returns KPP_OK, KPP_ERR_DEGENERATE (the data has fewer than min(K, passes)
  * distinct points; nothing is recorded), KPP_ERR_UNSUPPORTED (no candidate
  * could run in the given workspace) or kpp_seed's argument errors.
+ * If the environment variable KPP_TUNE_CACHE names a file, every winner is
+ * also appended to it as one text line keyed by the GPU model (name and SM
+ * count), dtype, d, N and K, and a process reads that file's lines for its
+ * GPU model once, at its first automatic choice on a device: later
+ * processes then use the recorded winners without tuning (a later line wins
+ * over an earlier one for the same shape).
  */
 KPP_API size_t kpp_tune_workspace_size(int64_t N, int32_t d, int32_t K, kpp_dtype dtype);
 KPP_API kpp_status kpp_tune(const void *points, const float *row_scales, int64_t N, int32_t d,
                             int32_t K, kpp_dtype dtype, int64_t *indices_out, float *d2_out,
                             void *workspace, size_t workspace_bytes, kpp_stream_t stream,
                             int32_t passes, kpp_options *best_out, float *best_ms_per_pass);
-/* Forgets every shape recorded by kpp_tune in this process. */
+/* Forgets every shape recorded by kpp_tune in this process, and what was
+ * read from a KPP_TUNE_CACHE file (which is not read again in this process;
+ * the file itself is left as it is). */
 KPP_API void kpp_tune_clear(void);
 
 /*

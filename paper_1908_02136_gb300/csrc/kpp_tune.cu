@@ -4,9 +4,12 @@
 // and records the winner for the automatic choice of later calls with the
 // same shape.  Host code only; every timed run is an ordinary kpp_seed call.
 #include <algorithm>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
+#include <string>
 #include <tuple>
 #include <vector>
 
@@ -28,6 +31,78 @@ struct TuneKey {
 
 std::mutex g_tune_mutex;
 std::map<TuneKey, kpp_options> g_tuned;
+
+// ---------------------------------------------------------------------------
+// Optional cache file (environment variable KPP_TUNE_CACHE = a path): every
+// winner is appended as one text line keyed by the GPU model (name and SM
+// count), dtype, d, N and K, and a process reads the lines of its GPU model
+// once, at its first automatic choice on a device, so that later processes
+// skip the tuning.  Later lines win over earlier ones for the same shape.
+// ---------------------------------------------------------------------------
+bool g_cache_read[64] = {};
+
+std::string device_model(int dev)
+{
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess)
+        return std::string();
+    std::string name(prop.name);
+    for (char &c : name)
+        if (c == ' ' || c == '\t')
+            c = '_';
+    return name + "/" + std::to_string(prop.multiProcessorCount);
+}
+
+// Appends one winner to the cache file (if the environment names one).
+void cache_append(int dev, int dt, int d, int64_t N, int32_t K, const kpp_options &o)
+{
+    const char *path = std::getenv("KPP_TUNE_CACHE");
+    if (!path || !*path)
+        return;
+    const std::string model = device_model(dev);
+    if (model.empty())
+        return;
+    FILE *f = std::fopen(path, "a");
+    if (!f)
+        return;
+    std::fprintf(f, "kpp-tune 1 %s %d %d %lld %d %d %d %d %d %d %d %d\n", model.c_str(), dt, d,
+                 (long long)N, K, o.form, o.lanes_per_row, o.ctas_per_sm, o.smem_cache,
+                 o.alternate, o.l2_policy, o.min_rows_per_cta);
+    std::fclose(f);
+}
+
+// Reads the cache file's lines for this device's model into g_tuned (once
+// per device and process; the caller holds g_tune_mutex).
+void cache_load(int dev)
+{
+    if (dev < 0 || dev >= 64 || g_cache_read[dev])
+        return;
+    g_cache_read[dev] = true;
+    const char *path = std::getenv("KPP_TUNE_CACHE");
+    if (!path || !*path)
+        return;
+    const std::string model = device_model(dev);
+    FILE *f = std::fopen(path, "r");
+    if (!f || model.empty()) {
+        if (f)
+            std::fclose(f);
+        return;
+    }
+    char line[512], m[256];
+    while (std::fgets(line, sizeof(line), f)) {
+        int ver = 0, dt = 0, d = 0, K = 0;
+        long long N = 0;
+        kpp_options o;
+        std::memset(&o, 0, sizeof(o));
+        if (std::sscanf(line, "kpp-tune %d %255s %d %d %lld %d %d %d %d %d %d %d %d", &ver, m, &dt,
+                        &d, &N, &K, &o.form, &o.lanes_per_row, &o.ctas_per_sm, &o.smem_cache,
+                        &o.alternate, &o.l2_policy, &o.min_rows_per_cta) != 13 ||
+            ver != 1 || model != m)
+            continue;
+        g_tuned[TuneKey{dev, dt, d, (int64_t)N, (int32_t)K}] = o;
+    }
+    std::fclose(f);
+}
 
 // The knobs the tuner sets are all zero: the caller asked for the automatic
 // choice.
@@ -86,6 +161,7 @@ bool tuned_options(int64_t N, int32_t d, int32_t K, int dt, const kpp_options &a
     if (cudaGetDevice(&dev) != cudaSuccess)
         return false;
     std::lock_guard<std::mutex> lock(g_tune_mutex);
+    cache_load(dev);
     auto it = g_tuned.find(TuneKey{dev, dt, d, N, K});
     if (it == g_tuned.end())
         return false;
@@ -119,6 +195,8 @@ void kpp_tune_clear(void)
 {
     std::lock_guard<std::mutex> lock(g_tune_mutex);
     g_tuned.clear();
+    for (bool &r : g_cache_read)
+        r = true; // what the cache file held is forgotten too, not read again
 }
 
 kpp_status kpp_tune(const void *points, const float *row_scales, int64_t N, int32_t d, int32_t K,
@@ -228,6 +306,7 @@ kpp_status kpp_tune(const void *points, const float *row_scales, int64_t N, int3
     {
         std::lock_guard<std::mutex> lock(g_tune_mutex);
         g_tuned[TuneKey{dev, (int)dtype, d, N, K}] = best;
+        cache_append(dev, (int)dtype, d, N, K, best);
     }
     *best_out = best;
     if (best_ms_per_pass)

@@ -94,3 +94,49 @@ def test_workspace_too_small_for_every_candidate():
                           ws.data_ptr(), ws.numel(),
                           ctypes.c_void_p(torch.cuda.current_stream().cuda_stream), 4, best)
     assert st == kpp.ERR_UNSUPPORTED
+
+
+_CACHE_CHILD = r"""
+import os, sys, json, numpy as np, torch
+sys.path.insert(0, os.getcwd())
+import paper_1908_02136_gb300 as kpp
+from paper_1908_02136_gb300 import datagen
+N, d, K = 20_011, 32, 24
+x = torch.from_numpy(datagen.integer_points(N, d, seed=N, n_comp=8)).to("cuda:0")
+if sys.argv[1] == "tune":
+    best, ms = kpp.tune(x, K, passes=8)
+    print(json.dumps({"best": best}))
+else:
+    st, p = kpp.kpp_describe(N, d, K, kpp.F32)
+    assert st == kpp.OK
+    print(json.dumps({"plan": [p.form, p.grid, p.lanes_per_row, p.rows_per_cta,
+                               p.cached_rows_per_cta]}))
+"""
+
+
+def test_tuning_cache_file_carries_the_winner_to_a_new_process(tmp_path):
+    """KPP_TUNE_CACHE: one process tunes and appends its winner to the file;
+    a second process, which does not tune, makes the same automatic choice."""
+    import json
+    import os
+    import subprocess
+    import sys
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    cache = tmp_path / "tune.txt"
+    env = dict(os.environ, KPP_TUNE_CACHE=str(cache))
+
+    def child(mode):
+        r = subprocess.run([sys.executable, "-c", _CACHE_CHILD, mode], capture_output=True,
+                           text=True, cwd=root, env=env, timeout=600)
+        assert r.returncode == 0, r.stderr[-3000:]
+        return json.loads(r.stdout.strip().splitlines()[-1])
+
+    best = child("tune")["best"]
+    lines = cache.read_text().splitlines()
+    assert len(lines) == 1 and lines[0].startswith("kpp-tune 1 ")
+    plan = child("describe")["plan"]
+    with torch.cuda.device(DEV):
+        st, p = kpp.kpp_describe(20_011, 32, 24, kpp.F32, best)
+    assert st == kpp.OK
+    assert plan == [p.form, p.grid, p.lanes_per_row, p.rows_per_cta, p.cached_rows_per_cta]
