@@ -379,6 +379,7 @@ __device__ __forceinline__ Pair pass_rows(const PassIO &io, const CentreRegs<DT,
                     }
                 }
             }
+            float part[G::JB];
 #pragma unroll
             for (int q = 0; q < G::JB; ++q) {
                 float a0 = 0.f, a1 = 0.f;
@@ -388,12 +389,37 @@ __device__ __forceinline__ Pair pass_rows(const PassIO &io, const CentreRegs<DT,
                     decode16<DT>(x[q][v], f);
                     cr.template accum<G::EPV>(f, v * G::EPV, sc[q], a0, a1);
                 }
-                float part = a0 + a1;
+                part[q] = a0 + a1;
+            }
+            if constexpr (G::JB == G::L) {
+                // every slot of the row group is in this batch: reduce-scatter
+                // over the L lanes sharing the rows -- halving the live slots
+                // at each step, each lane keeping the half its bit selects --
+                // leaves slot l's sum on lane l.  Each lane adds the same
+                // partials in the same pairs as the butterfly below, so the
+                // sums are bit-identical to it, with log2(L) shuffle rounds
+                // for all L rows instead of log2(L) per row.
 #pragma unroll
-                for (int o = G::L / 2; o > 0; o >>= 1)
-                    part += __shfl_xor_sync(0xffffffffu, part, o);
-                if (l == jb + q)
-                    mine = part;
+                for (int o = G::L / 2, n = G::JB; o > 0; o >>= 1, n >>= 1) {
+                    const bool up = (l & o) != 0;
+#pragma unroll
+                    for (int i = 0; i < n / 2; ++i) {
+                        const float send = up ? part[i] : part[i + n / 2];
+                        const float keep = up ? part[i + n / 2] : part[i];
+                        part[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+                    }
+                }
+                mine = part[0];
+            } else {
+#pragma unroll
+                for (int q = 0; q < G::JB; ++q) {
+                    float sum = part[q];
+#pragma unroll
+                    for (int o = G::L / 2; o > 0; o >>= 1)
+                        sum += __shfl_xor_sync(0xffffffffu, sum, o);
+                    if (l == jb + q)
+                        mine = sum;
+                }
             }
             if (jb + G::JB == G::L) { // last batch of the super-iteration
                 const int64_t own_row = rb + (int64_t)l * (32 / G::L) + g;
