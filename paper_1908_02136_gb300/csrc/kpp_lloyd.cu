@@ -19,6 +19,7 @@
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 
@@ -40,6 +41,11 @@ constexpr int kMaxStages = 4; // centre-tile stages in flight
 constexpr uint32_t kTmemCols = 2 * kMT * kBN; // [buffer][point tile] accumulators: 512
 constexpr uint32_t kABytes = kBM * kBK * 2; // one plane, one chunk: 16 KB
 constexpr uint32_t kBBytes = kBN * kBK * 2; // 16 KB
+// The CTA-pair form: 256-point x 256-centre tiles over two SMs, each CTA
+// holding 128 points and 128 centres (one kBBytes plane each) of a tile.
+constexpr int kPN = 256;     // centres per tile: accumulator columns in each CTA
+constexpr int kPNH = kPN / 2; // centres per tile held by each CTA
+constexpr int kMaxStagesPair = 8;
 constexpr size_t kAlign = 256;
 
 size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
@@ -168,6 +174,32 @@ struct AssignArgs {
     uint64_t timeout_ns;
 };
 
+// The smallest of 32 scores and its position, the first one on ties: a
+// tournament in which the later of two entries wins only when strictly
+// smaller.  Depth 5 instead of a 32-long chain of dependent compares, so the
+// four epilogue warps keep their issue slots busy.
+__device__ __forceinline__ float block_argmin32(float (&w)[32], int &wi)
+{
+    int id[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+        const bool p = w[2 * j + 1] < w[2 * j];
+        w[j] = p ? w[2 * j + 1] : w[2 * j];
+        id[j] = 2 * j + (p ? 1 : 0);
+    }
+#pragma unroll
+    for (int n = 8; n >= 1; n >>= 1) {
+#pragma unroll
+        for (int j = 0; j < n; ++j) {
+            const bool p = w[2 * j + 1] < w[2 * j];
+            w[j] = p ? w[2 * j + 1] : w[2 * j];
+            id[j] = p ? id[2 * j + 1] : id[2 * j];
+        }
+    }
+    wi = id[0];
+    return w[0];
+}
+
 __device__ __forceinline__ void fail(Control *ctl, volatile int *abort_flag)
 {
     *abort_flag = 1;
@@ -180,7 +212,8 @@ __device__ __forceinline__ void fail(Control *ctl, volatile int *abort_flag)
 // shared-memory stages; each stage feeds the MMAs of all kMT point tiles, so
 // a centre byte read from L2 serves 256 points.  The MMA thread accumulates
 // hi.hi + hi.lo + lo.hi into one of two sets of tensor-memory accumulators;
-// the four epilogue warps turn a finished set into running argmins while the
+// the four epilogue warps turn a finished set into running argmins (a
+// tournament per 32-column block, then one compare per block) while the
 // next one fills.  Every wait is bounded: on a timeout the kernel records
 // KPP_ERR_TIMEOUT, lets the copies and MMAs already issued finish (again
 // bounded), frees its tensor memory and returns.
@@ -380,19 +413,20 @@ __global__ void __launch_bounds__(kThreads, 1)
                         tmem_regs_ready(r[1]);
 #pragma unroll
                         for (int c = 0; c < 2; ++c) {
+                            float w[32];
 #pragma unroll
                             for (int v = 0; v < 8; ++v) {
                                 const float4 n4 = cn4[(h + c) * 8 + v];
-                                const float nv[4] = {n4.x, n4.y, n4.z, n4.w};
-#pragma unroll
-                                for (int e = 0; e < 4; ++e) {
-                                    const int i = v * 4 + e;
-                                    const float sc = fmaf(-2.f, __uint_as_float(r[c][i]), nv[e]);
-                                    if (sc < best[mt]) {
-                                        best[mt] = sc;
-                                        bk[mt] = ct * kBN + (h + c) * 32 + i;
-                                    }
-                                }
+                                w[v * 4 + 0] = fmaf(-2.f, __uint_as_float(r[c][v * 4 + 0]), n4.x);
+                                w[v * 4 + 1] = fmaf(-2.f, __uint_as_float(r[c][v * 4 + 1]), n4.y);
+                                w[v * 4 + 2] = fmaf(-2.f, __uint_as_float(r[c][v * 4 + 2]), n4.z);
+                                w[v * 4 + 3] = fmaf(-2.f, __uint_as_float(r[c][v * 4 + 3]), n4.w);
+                            }
+                            int wi;
+                            const float m = block_argmin32(w, wi);
+                            if (m < best[mt]) { // earlier blocks win ties
+                                best[mt] = m;
+                                bk[mt] = ct * kBN + (h + c) * 32 + wi;
                             }
                         }
                     }
@@ -415,6 +449,259 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (warp == 2) {
         fence_after_sync();
         tmem_dealloc(tmem, kTmemCols);
+    }
+}
+
+// The same assignment on CTA pairs (clusters of two CTAs on neighbouring
+// SMs).  One thread of the even CTA issues tcgen05.mma.cta_group::2 with
+// M = N = 256: A is the two CTAs' own 128-point tiles, B a 256-centre tile of
+// which each CTA holds half (centres 0-127 of the tile in the even CTA,
+// 128-255 in the odd one), and each CTA's tensor memory receives its points'
+// 256 scores.  Per SM every MMA then does 128 x 256 x 16 multiply-adds from
+// 8 KB of shared-memory operands (the one-SM form's 128 x 128 x 16 MMAs
+// read as much for half the work), and half as many MMAs are issued.
+//
+// Protocol: both CTAs' loads complete on the even CTA's full barriers (which
+// its producer arms with the pair's byte count); each MMA commit arrives on
+// the barrier at the same offset in both CTAs (stage free, accumulator
+// ready, point buffer free); each epilogue warp of either CTA releases an
+// accumulator with one arrival on the even CTA's barrier.  Every wait is
+// bounded; after a timeout the MMAs already issued are drained, loads in
+// flight are given 200 us to land, and the pair frees its tensor memory
+// together.
+__global__ void __launch_bounds__(kThreads, 1)
+    lloyd_assign_pair_kernel(const __grid_constant__ CUtensorMap map_phi,
+                             const __grid_constant__ CUtensorMap map_plo,
+                             const __grid_constant__ CUtensorMap map_chi,
+                             const __grid_constant__ CUtensorMap map_clo, AssignArgs a)
+{
+    using namespace tc;
+    const int K = a.Kdev ? *a.Kdev : a.K;
+    if (K <= 0)
+        return; // nothing to assign (every thread of every CTA leaves before any setup)
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                                ~uintptr_t(1023));
+    const int NS = a.stages;
+    const uint32_t abytes = 2 * a.nk * kABytes; // this CTA's point tile, both planes
+    uint8_t *sA = smem;                         // [buffer][plane][chunk] 16 KB each
+    uint8_t *sB = smem + a.abufs * abytes;      // [stage][plane] 16 KB each
+    float *s_cn = reinterpret_cast<float *>(sB + NS * 2 * kBBytes);
+    __shared__ uint64_t a_full[2], a_empty[2], b_full[kMaxStagesPair], b_empty[kMaxStagesPair],
+        acc_full[2], acc_empty[2], done;
+    __shared__ uint32_t tmem_base;
+    __shared__ volatile int abort_flag;
+    auto a_tile = [&](uint32_t b, int plane, int k) {
+        return sA + b * abytes + (plane * a.nk + k) * kABytes;
+    };
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t rank = cluster_rank(); // 0 issues the MMAs
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < 2; ++s) {
+            mbar_init(&a_full[s], 1);
+            mbar_init(&a_empty[s], 1);
+            mbar_init(&acc_full[s], 1);
+            mbar_init(&acc_empty[s], 2 * 4); // each epilogue warp of both CTAs
+        }
+        for (int s = 0; s < NS; ++s) {
+            mbar_init(&b_full[s], 1);
+            mbar_init(&b_empty[s], 1);
+        }
+        mbar_init(&done, 1);
+        fence_mbar_init();
+        abort_flag = 0;
+    }
+    const int n_ct = (K + kPN - 1) / kPN;
+    for (int k = threadIdx.x; k < n_ct * kPN; k += blockDim.x)
+        s_cn[k] = k < K ? a.cn[k] : __int_as_float(0x7f800000);
+    // both CTAs running with their barriers initialised before any signal
+    // crosses between them and before they allocate tensor memory together
+    cluster_sync();
+    if (warp == 2)
+        tmem_alloc_pair(&tmem_base, kTmemCols);
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+
+    const int64_t n_mt = (a.N + kBM - 1) / kBM;
+    const int64_t n_grp = (n_mt + 1) / 2; // 256-point groups of the pair
+    const int64_t cl0 = cluster_id_x(), ncl = n_clusters_x();
+    const uint32_t tmem = tmem_base;
+
+    if (warp == 0 && lane == 0) {
+        // ---- producer (both CTAs): own point tile, own half of each centre tile ----
+        uint32_t it = 0, g = 0;
+        for (int64_t gp = cl0; gp < n_grp && !abort_flag; gp += ncl, ++it) {
+            const uint32_t ab = it % a.abufs, ause = it / a.abufs;
+            if (ause > 0 && !mbar_wait_cluster(&a_empty[ab], (ause - 1) & 1, a.timeout_ns)) {
+                fail(a.ctl, &abort_flag);
+                break;
+            }
+            if (rank == 0)
+                mbar_expect_tx(&a_full[ab], 2 * abytes);
+            const uint32_t fa = mapa(smem_u32(&a_full[ab]), 0);
+            const int y = (int)((gp * 2 + rank) * kBM);
+            for (int k = 0; k < a.nk; ++k) {
+                tma_load_2d_pair(a_tile(ab, 0, k), &map_phi, fa, k * kBK, y);
+                tma_load_2d_pair(a_tile(ab, 1, k), &map_plo, fa, k * kBK, y);
+            }
+            for (int ct = 0; ct < n_ct && !abort_flag; ++ct) {
+                for (int k = 0; k < a.nk; ++k, ++g) {
+                    const uint32_t s = g % NS, use = g / NS;
+                    if (use > 0 && !mbar_wait_cluster(&b_empty[s], (use - 1) & 1, a.timeout_ns)) {
+                        fail(a.ctl, &abort_flag);
+                        break;
+                    }
+                    if (rank == 0)
+                        mbar_expect_tx(&b_full[s], 2 * 2 * kBBytes);
+                    const uint32_t fb = mapa(smem_u32(&b_full[s]), 0);
+                    const int yc = ct * kPN + (int)rank * kPNH;
+                    tma_load_2d_pair(sB + (s * 2 + 0) * kBBytes, &map_chi, fb, k * kBK, yc);
+                    tma_load_2d_pair(sB + (s * 2 + 1) * kBBytes, &map_clo, fb, k * kBK, yc);
+                }
+            }
+        }
+        if (abort_flag) {
+            // this CTA's loads complete on the even CTA's barriers, which
+            // this thread cannot wait on: give those in flight time to land
+            const uint64_t t0 = gtimer();
+            while (gtimer() - t0 < 200000ull)
+                __nanosleep(1000);
+        }
+    } else if (warp == 1 && lane == 0 && rank == 0) {
+        // ---- MMA issuer (even CTA) ----
+        const uint32_t idesc = idesc_bf16_f32(2 * kBM, kPN);
+        uint32_t it = 0, g = 0, t = 0;
+        bool issued = false;
+        for (int64_t gp = cl0; gp < n_grp && !abort_flag; gp += ncl, ++it) {
+            const uint32_t ab = it % a.abufs, ause = it / a.abufs;
+            if (!mbar_wait_cluster(&a_full[ab], ause & 1, a.timeout_ns)) {
+                fail(a.ctl, &abort_flag);
+                break;
+            }
+            fence_after_sync();
+            for (int ct = 0; ct < n_ct && !abort_flag; ++ct, ++t) {
+                const uint32_t buf = t & 1, use_acc = t >> 1;
+                if (use_acc > 0 &&
+                    !mbar_wait_cluster(&acc_empty[buf], (use_acc - 1) & 1, a.timeout_ns)) {
+                    fail(a.ctl, &abort_flag);
+                    break;
+                }
+                fence_after_sync();
+                const uint32_t d_tmem = tmem + buf * kPN;
+                for (int k = 0; k < a.nk; ++k, ++g) {
+                    const uint32_t s = g % NS, use = g / NS;
+                    if (!mbar_wait_cluster(&b_full[s], use & 1, a.timeout_ns)) {
+                        fail(a.ctl, &abort_flag);
+                        break;
+                    }
+                    fence_after_sync();
+                    const uint32_t bh = smem_u32(sB + (s * 2 + 0) * kBBytes);
+                    const uint32_t bl = smem_u32(sB + (s * 2 + 1) * kBBytes);
+                    const uint32_t ah = smem_u32(a_tile(ab, 0, k));
+                    const uint32_t al = smem_u32(a_tile(ab, 1, k));
+#pragma unroll
+                    for (int kk = 0; kk < kBK / 16; ++kk) {
+                        const uint32_t o = kk * 32;
+                        mma_bf16_pair(d_tmem, sdesc_k_sw128(ah + o), sdesc_k_sw128(bh + o), idesc,
+                                      (k | kk) ? 1u : 0u);
+                        mma_bf16_pair(d_tmem, sdesc_k_sw128(ah + o), sdesc_k_sw128(bl + o), idesc,
+                                      1u);
+                        mma_bf16_pair(d_tmem, sdesc_k_sw128(al + o), sdesc_k_sw128(bh + o), idesc,
+                                      1u);
+                    }
+                    issued = true;
+                    mma_commit_pair(&b_empty[s], 0x3); // both halves of stage s are free
+                }
+                if (abort_flag)
+                    break;
+                mma_commit_pair(&acc_full[buf], 0x3);
+            }
+            if (abort_flag)
+                break;
+            mma_commit_pair(&a_empty[ab], 0x3);
+        }
+        if (issued) { // every MMA issued completes before the pair frees its tensor memory
+            mma_commit_pair(&done, 0x1);
+            mbar_wait_cluster(&done, 0, a.timeout_ns);
+        }
+    } else if (warp >= 4) {
+        // ---- epilogue (both CTAs): its own 128 rows of each accumulator ----
+        const int q = warp & 3;
+        const int row_local = q * 32 + lane;
+        uint32_t t = 0;
+        for (int64_t gp = cl0; gp < n_grp && !abort_flag; gp += ncl) {
+            float best = __int_as_float(0x7f800000);
+            int bk = 0;
+            for (int ct = 0; ct < n_ct; ++ct, ++t) {
+                const uint32_t buf = t & 1, use = t >> 1;
+                if (!mbar_wait_cluster(&acc_full[buf], use & 1, a.timeout_ns)) {
+                    fail(a.ctl, &abort_flag);
+                    break;
+                }
+                fence_after_sync();
+                const float4 *cn4 = reinterpret_cast<const float4 *>(s_cn + ct * kPN);
+                // four rounds of 64 columns; the next round's loads are in
+                // flight while this one is scored
+                const uint32_t base = tmem + buf * kPN + ((uint32_t)(q * 32) << 16);
+                uint32_t r[2][2][32];
+                tmem_ld32_async(base, r[0][0]);
+                tmem_ld32_async(base + 32, r[0][1]);
+                tmem_ld_wait();
+                tmem_regs_ready(r[0][0]);
+                tmem_regs_ready(r[0][1]);
+#pragma unroll
+                for (int j = 0; j < kPN / 64; ++j) {
+                    const int slot = j & 1, h = 2 * j;
+                    if (j + 1 < kPN / 64) {
+                        tmem_ld32_async(base + (h + 2) * 32, r[slot ^ 1][0]);
+                        tmem_ld32_async(base + (h + 3) * 32, r[slot ^ 1][1]);
+                    }
+#pragma unroll
+                    for (int c = 0; c < 2; ++c) {
+                        float w[32];
+#pragma unroll
+                        for (int v = 0; v < 8; ++v) {
+                            const float4 n4 = cn4[(h + c) * 8 + v];
+                            w[v * 4 + 0] = fmaf(-2.f, __uint_as_float(r[slot][c][v * 4 + 0]), n4.x);
+                            w[v * 4 + 1] = fmaf(-2.f, __uint_as_float(r[slot][c][v * 4 + 1]), n4.y);
+                            w[v * 4 + 2] = fmaf(-2.f, __uint_as_float(r[slot][c][v * 4 + 2]), n4.z);
+                            w[v * 4 + 3] = fmaf(-2.f, __uint_as_float(r[slot][c][v * 4 + 3]), n4.w);
+                        }
+                        int wi;
+                        const float m = block_argmin32(w, wi);
+                        if (m < best) { // earlier blocks win ties
+                            best = m;
+                            bk = ct * kPN + (h + c) * 32 + wi;
+                        }
+                    }
+                    if (j + 1 < kPN / 64) {
+                        tmem_ld_wait();
+                        tmem_regs_ready(r[slot ^ 1][0]);
+                        tmem_regs_ready(r[slot ^ 1][1]);
+                    }
+                }
+                fence_before_sync();
+                __syncwarp();
+                if (lane == 0)
+                    mbar_arrive_cluster(mapa(smem_u32(&acc_empty[buf]), 0));
+            }
+            if (abort_flag)
+                break;
+            const int64_t row = (gp * 2 + rank) * kBM + row_local;
+            if (row < a.N)
+                a.labels[row] = bk;
+        }
+    }
+    // the pair's MMAs drained (the even CTA waited for them) and both
+    // epilogues done before either CTA frees tensor memory or exits
+    fence_before_sync();
+    __syncthreads();
+    cluster_sync();
+    if (warp == 2) {
+        fence_after_sync();
+        tmem_dealloc_pair(tmem, kTmemCols);
     }
 }
 
@@ -663,6 +950,43 @@ int assign_stages(int nk, int K, int abufs)
 constexpr int kMinStagesTwoA = 2;
 int assign_abufs(int nk, int K) { return assign_stages(nk, K, 2) >= kMinStagesTwoA ? 2 : 1; }
 
+// The CTA-pair form's centre stages (half a 256-centre tile each) and point
+// buffers (one 128-point tile each).
+int padded_k_pair(int K) { return (K + kPN - 1) / kPN * kPN; }
+int assign_stages_pair(int nk, int K, int abufs)
+{
+    const long long budget = 227LL * 1024 - 1024 - 8 * 1024 -
+                             (long long)abufs * 2 * nk * kABytes - (long long)padded_k_pair(K) * 4;
+    const int s = budget > 0 ? (int)(budget / (2 * kBBytes)) : 0;
+    return s < kMaxStagesPair ? s : kMaxStagesPair;
+}
+constexpr int kMinStagesTwoAPair = 3;
+int assign_abufs_pair(int nk, int K)
+{
+    return assign_stages_pair(nk, K, 2) >= kMinStagesTwoAPair ? 2 : 1;
+}
+size_t assign_smem_pair(int nk, int K)
+{
+    const int ab = assign_abufs_pair(nk, K);
+    return 1024 + (size_t)ab * 2 * nk * kABytes + (size_t)assign_stages_pair(nk, K, ab) * 2 * kBBytes +
+           (size_t)padded_k_pair(K) * 4;
+}
+
+// Which assignment kernel: the CTA-pair form above 64 features (two
+// feature chunks, where the MMAs dominate and its wider MMAs pay), the
+// one-SM form at or below (where the epilogue does; measured 10^7 points,
+// K = 1024: 5.0 against 5.5 ms at d = 128, 3.9 against 3.1 ms at d = 64).
+// KPP_LLOYD_PAIR=0 or 1 forces one of them; both give the same labels.
+bool use_pair_form(int nk)
+{
+    const char *e = std::getenv("KPP_LLOYD_PAIR");
+    if (e && e[0] == '0')
+        return false;
+    if (e && e[0] == '1')
+        return true;
+    return nk > 1;
+}
+
 size_t assign_smem(int nk, int K)
 {
     const int ab = assign_abufs(nk, K);
@@ -731,6 +1055,43 @@ kpp_status assign_impl(const float *centres, const long long *row0, const int32_
         split_rows_kernel<<<(K * L.dp / 8 + 255) / 256, 256, 0, s>>>(centres, K, d, L.dp, chi,
                                                                      clo);
         centre_norms_kernel<<<(K + 127) / 128, 128, 0, s>>>(centres, K, d, cn);
+    }
+    if (use_pair_form(nk)) {
+        // CTA pairs: persistent, as many clusters of two as fit at once
+        AssignArgs a2 = a;
+        a2.abufs = assign_abufs_pair(nk, K);
+        a2.stages = assign_stages_pair(nk, K, a2.abufs);
+        const size_t smem2 = assign_smem_pair(nk, K);
+        if (a2.stages >= 2 &&
+            cudaFuncSetAttribute(lloyd_assign_pair_kernel,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem2) == cudaSuccess) {
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeClusterDimension;
+            attr[0].val.clusterDim.x = 2;
+            attr[0].val.clusterDim.y = 1;
+            attr[0].val.clusterDim.z = 1;
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3(2, 1, 1);
+            cfg.blockDim = dim3(kThreads, 1, 1);
+            cfg.dynamicSmemBytes = smem2;
+            cfg.stream = s;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            int ncl = 0;
+            if (cudaOccupancyMaxActiveClusters(&ncl, lloyd_assign_pair_kernel, &cfg) ==
+                    cudaSuccess &&
+                ncl >= 1) {
+                const int64_t n_grp2 = ((N + kBM - 1) / kBM + 1) / 2;
+                const int64_t clusters = n_grp2 < ncl ? n_grp2 : ncl;
+                cfg.gridDim = dim3((unsigned)(2 * clusters), 1, 1);
+                if (cudaLaunchKernelEx(&cfg, lloyd_assign_pair_kernel, m_phi, m_plo, m_chi, m_clo,
+                                       a2) != cudaSuccess)
+                    return KPP_ERR_LAUNCH;
+                return cudaGetLastError() == cudaSuccess ? KPP_OK : KPP_ERR_LAUNCH;
+            }
+        }
+        (void)cudaGetLastError(); // no cluster fits: the one-SM form below
     }
     const int64_t n_grp = ((N + kBM - 1) / kBM + kMT - 1) / kMT;
     const int grid = (int)(n_grp < sms ? n_grp : sms);

@@ -137,3 +137,45 @@ def test_argument_errors():
                                 torch.empty_like(c).data_ptr(), None, None, small.data_ptr(),
                                 small.numel(), None)
     assert st == kpp.ERR_WORKSPACE
+
+
+@pytest.mark.parametrize("N,d,K", [(127, 16, 5), (1000, 8, 7), (200_003, 32, 1000),
+                                   (150_000, 128, 300), (100_000, 64, 4096), (70_001, 100, 257)])
+def test_pair_and_single_sm_forms_agree(N, d, K, monkeypatch):
+    """The CTA-pair assignment (256 x 256 MMAs over two SMs, the default above 64 features)
+    and the one-SM kernel add the same products per score in the same
+    order, so their labels are identical: float data, ragged N (a pair whose
+    second CTA has no points), K over partial and many centre tiles, both
+    feature chunks, and N large enough that every cluster reuses its point
+    buffers and centre stages."""
+    x_np = datagen.gmm(N, d, min(K, 64), seed=N % 97)
+    C = torch.from_numpy(x_np[np.random.default_rng(2).choice(N, K, replace=False)]).to(DEV)
+    ll = kpp.Lloyd(torch.from_numpy(x_np).to(DEV), K)
+    monkeypatch.setenv("KPP_LLOYD_PAIR", "0")
+    single = ll.assign(C).cpu().numpy()
+    monkeypatch.setenv("KPP_LLOYD_PAIR", "1")
+    pair = ll.assign(C).cpu().numpy()
+    assert np.array_equal(pair, single)
+    # and the pair form against the oracle on a sample of points
+    rows = np.random.default_rng(3).choice(N, min(N, 2000), replace=False)
+    C64 = C.cpu().numpy().astype(np.float64)
+    ref = oracle.lloyd_step(x_np[rows], C64)
+    X = x_np[rows].astype(np.float64)
+    dist_g = ((X - C64[pair[rows]]) ** 2).sum(1)
+    diff = pair[rows] != ref["labels"]
+    scale = np.linalg.norm(X, axis=1) * np.linalg.norm(C64, axis=1).max() + 1e-30
+    assert np.all((dist_g[diff] - ref["d2"][diff]) / scale[diff] <= LABEL_BOUND)
+    assert diff.sum() <= max(2, MAX_EVENT_FRAC * rows.size)
+
+
+def test_pair_form_integer_regime_bit_identical(monkeypatch):
+    """Integer coordinates over many groups per cluster: the pair form's
+    labels equal the oracle's exactly."""
+    monkeypatch.setenv("KPP_LLOYD_PAIR", "1")
+    N, d, K = 300_000, 48, 700
+    x = datagen.integer_points(N, d, seed=5, n_comp=16)
+    C = x[np.random.default_rng(4).choice(N, K, replace=False)].astype(np.float64)
+    lab, d2, C2, cnt, phi = _step(x, C)
+    ref = oracle.lloyd_step(x, C)
+    assert np.array_equal(lab, ref["labels"])
+    assert np.array_equal(cnt, ref["counts"])
