@@ -551,6 +551,11 @@ def run_lloyd(args, rank, world, dev, pg, barrier):
     from paper_1908_02136_gb300 import datagen, multi
 
     wl = datagen.WORKLOADS[args.workload[len(LLOYD_PREFIX):]]
+    if args.n_points or args.k_seeds:  # a smaller instance of the same recipe (profiling)
+        import dataclasses
+
+        n_, k_ = args.n_points or wl.N, args.k_seeds or wl.K
+        wl = dataclasses.replace(wl, N=n_, K=k_, name=f"{wl.name}@N{n_}K{k_}")
     x = datagen.workload_points(wl, dev)
     N, d, K = wl.N, wl.d, wl.K
     stream = torch.cuda.Stream(dev)
@@ -640,14 +645,15 @@ def run_lloyd(args, rank, world, dev, pg, barrier):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": args.workload, "N": N, "d": d, "K": K,
-                       "assignment": "tcgen05 BF16 split (hi.hi + hi.lo + lo.hi), FP32 accumulate",
+                       "assignment": "tcgen05 BF16 split (hi.hi + hi.lo + lo.hi), FP32 accumulate, "
+                                     "CTA pairs (cta_group::2, 256 x 256 tiles)",
                        "assign_ms": a_ms, "parallelism": f"replicas{world}",
                        "l2": "flushed between steps (512 MiB write)",
                        "phi": float(phi.item())},
             "clocks": clocks, "e2e": None, "gpu_launches": 5 * args.steps,
             "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak,
                          "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                         "kernel": "lloyd_assign_kernel",
+                         "kernel": "lloyd_assign_pair_kernel",
                          "tensor_flops_per_launch": tensor_flops,
                          "algorithmic_flops_per_launch": 2.0 * nkd,
                          "peak_source": "measured bf16 (burst)" if peaks else "fallback"},
@@ -765,7 +771,7 @@ def run_kmpar(args, rank, world, dev, pg, barrier):
             "clocks": clocks, "e2e": None, "gpu_launches": launches * args.steps,
             "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak,
                          "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                         "kernel": "lloyd_assign_kernel",
+                         "kernel": "lloyd_assign_pair_kernel",
                          "launch": f"kpp_lloyd_assign, N={N}, K={ke} candidates",
                          "tensor_flops_per_launch": tensor_flops,
                          "peak_source": "measured bf16 (burst)" if peaks else "fallback"},

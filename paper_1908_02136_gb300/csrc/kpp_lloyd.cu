@@ -972,19 +972,14 @@ size_t assign_smem_pair(int nk, int K)
            (size_t)padded_k_pair(K) * 4;
 }
 
-// Which assignment kernel: the CTA-pair form above 64 features (two
-// feature chunks, where the MMAs dominate and its wider MMAs pay), the
-// one-SM form at or below (where the epilogue does; measured 10^7 points,
-// K = 1024: 5.0 against 5.5 ms at d = 128, 3.9 against 3.1 ms at d = 64).
-// KPP_LLOYD_PAIR=0 or 1 forces one of them; both give the same labels.
-bool use_pair_form(int nk)
+// Which assignment kernel: the CTA-pair form wherever a cluster of two fits
+// (measured on 10^7 points, K = 1024: 2.89 against 3.10 ms at d = 64, 4.65
+// against 5.55 ms at d = 128); the one-SM form otherwise.  KPP_LLOYD_PAIR=0
+// or 1 forces one of them; both give the same labels.
+bool use_pair_form()
 {
     const char *e = std::getenv("KPP_LLOYD_PAIR");
-    if (e && e[0] == '0')
-        return false;
-    if (e && e[0] == '1')
-        return true;
-    return nk > 1;
+    return !(e && e[0] == '0');
 }
 
 size_t assign_smem(int nk, int K)
@@ -1056,7 +1051,7 @@ kpp_status assign_impl(const float *centres, const long long *row0, const int32_
                                                                      clo);
         centre_norms_kernel<<<(K + 127) / 128, 128, 0, s>>>(centres, K, d, cn);
     }
-    if (use_pair_form(nk)) {
+    if (use_pair_form()) {
         // CTA pairs: persistent, as many clusters of two as fit at once
         AssignArgs a2 = a;
         a2.abufs = assign_abufs_pair(nk, K);

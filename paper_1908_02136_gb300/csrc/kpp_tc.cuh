@@ -221,11 +221,13 @@ __device__ __forceinline__ uint32_t mapa(uint32_t saddr, uint32_t rank)
     asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(saddr), "r"(rank));
     return r;
 }
-// One arrival on a barrier of any CTA of the cluster (shared::cluster address).
+// One arrival on a barrier of any CTA of the cluster (shared::cluster
+// address), with the default (CTA-scope release) semantics: what it orders
+// here is tensor-memory reads, which tcgen05.fence::before_thread_sync
+// already places before it, so no cluster-wide fence is paid per arrival.
 __device__ __forceinline__ void mbar_arrive_cluster(uint32_t caddr)
 {
-    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(caddr)
-                 : "memory");
+    asm volatile("mbarrier.arrive.shared::cluster.b64 _, [%0];" ::"r"(caddr) : "memory");
 }
 // mbar_wait with cluster-scope acquire: for barriers that other CTAs of the
 // cluster (or their copies and MMAs) complete.

@@ -142,7 +142,7 @@ def test_argument_errors():
 @pytest.mark.parametrize("N,d,K", [(127, 16, 5), (1000, 8, 7), (200_003, 32, 1000),
                                    (150_000, 128, 300), (100_000, 64, 4096), (70_001, 100, 257)])
 def test_pair_and_single_sm_forms_agree(N, d, K, monkeypatch):
-    """The CTA-pair assignment (256 x 256 MMAs over two SMs, the default above 64 features)
+    """The CTA-pair assignment (256 x 256 MMAs over two SMs, the default)
     and the one-SM kernel add the same products per score in the same
     order, so their labels are identical: float data, ragged N (a pair whose
     second CTA has no points), K over partial and many centre tiles, both
