@@ -354,6 +354,10 @@ KPP_API void kpp_tune_clear(void);
  * the split of the points into the workspace; call it again whenever the
  * points change.  Asynchronous on `stream`; a bounded wait that gave up is
  * reported as KPP_ERR_TIMEOUT by kpp_read_status(workspace).
+ * The assignment runs on clusters of two CTAs sharing each MMA
+ * (tcgen05 cta_group::2) wherever such a cluster can be launched, else on
+ * one SM per CTA; the environment variable KPP_LLOYD_PAIR=0 selects the
+ * one-SM kernel.  Both give the same labels.
  */
 KPP_API size_t kpp_lloyd_workspace_size(int64_t N, int32_t d, int32_t K);
 KPP_API kpp_status kpp_lloyd_prepare(const float *points, int64_t N, int32_t d, int32_t K,
