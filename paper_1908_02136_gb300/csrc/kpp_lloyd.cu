@@ -200,6 +200,28 @@ __device__ __forceinline__ float block_argmin32(float (&w)[32], int &wi)
     return w[0];
 }
 
+// The 32 scores |c_k|^2 - 2 x.c_k of a block from the accumulators `acc`
+// (x.c_k, FP32 bits) and the norms `n4` (eight float4), two per packed FP32
+// fma (each lane rounded as fmaf(-2, x.c, |c|^2)).
+__device__ __forceinline__ void block_scores32(const uint32_t (&acc)[32], const float4 *n4,
+                                               float (&w)[32])
+{
+    const uint64_t m2 = 0xC0000000C0000000ull; // {-2.f, -2.f}
+#pragma unroll
+    for (int v = 0; v < 8; ++v) {
+        const float4 n = n4[v];
+        uint64_t a01, a23, n01, n23, s01, s23;
+        asm("mov.b64 %0, {%1, %2};" : "=l"(a01) : "r"(acc[4 * v + 0]), "r"(acc[4 * v + 1]));
+        asm("mov.b64 %0, {%1, %2};" : "=l"(a23) : "r"(acc[4 * v + 2]), "r"(acc[4 * v + 3]));
+        asm("mov.b64 %0, {%1, %2};" : "=l"(n01) : "f"(n.x), "f"(n.y));
+        asm("mov.b64 %0, {%1, %2};" : "=l"(n23) : "f"(n.z), "f"(n.w));
+        asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(s01) : "l"(m2), "l"(a01), "l"(n01));
+        asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(s23) : "l"(m2), "l"(a23), "l"(n23));
+        asm("mov.b64 {%0, %1}, %2;" : "=f"(w[4 * v + 0]), "=f"(w[4 * v + 1]) : "l"(s01));
+        asm("mov.b64 {%0, %1}, %2;" : "=f"(w[4 * v + 2]), "=f"(w[4 * v + 3]) : "l"(s23));
+    }
+}
+
 __device__ __forceinline__ void fail(Control *ctl, volatile int *abort_flag)
 {
     *abort_flag = 1;
@@ -414,14 +436,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
                         for (int c = 0; c < 2; ++c) {
                             float w[32];
-#pragma unroll
-                            for (int v = 0; v < 8; ++v) {
-                                const float4 n4 = cn4[(h + c) * 8 + v];
-                                w[v * 4 + 0] = fmaf(-2.f, __uint_as_float(r[c][v * 4 + 0]), n4.x);
-                                w[v * 4 + 1] = fmaf(-2.f, __uint_as_float(r[c][v * 4 + 1]), n4.y);
-                                w[v * 4 + 2] = fmaf(-2.f, __uint_as_float(r[c][v * 4 + 2]), n4.z);
-                                w[v * 4 + 3] = fmaf(-2.f, __uint_as_float(r[c][v * 4 + 3]), n4.w);
-                            }
+                            block_scores32(r[c], cn4 + (h + c) * 8, w);
                             int wi;
                             const float m = block_argmin32(w, wi);
                             if (m < best[mt]) { // earlier blocks win ties
@@ -657,18 +672,18 @@ __global__ void __launch_bounds__(kThreads, 1)
                     if (j + 1 < kPN / 64) {
                         tmem_ld32_async(base + (h + 2) * 32, r[slot ^ 1][0]);
                         tmem_ld32_async(base + (h + 3) * 32, r[slot ^ 1][1]);
+                    } else {
+                        // every column of the accumulator is in registers:
+                        // release it before scoring the last 64
+                        fence_before_sync();
+                        __syncwarp();
+                        if (lane == 0)
+                            mbar_arrive_cluster(mapa(smem_u32(&acc_empty[buf]), 0));
                     }
 #pragma unroll
                     for (int c = 0; c < 2; ++c) {
                         float w[32];
-#pragma unroll
-                        for (int v = 0; v < 8; ++v) {
-                            const float4 n4 = cn4[(h + c) * 8 + v];
-                            w[v * 4 + 0] = fmaf(-2.f, __uint_as_float(r[slot][c][v * 4 + 0]), n4.x);
-                            w[v * 4 + 1] = fmaf(-2.f, __uint_as_float(r[slot][c][v * 4 + 1]), n4.y);
-                            w[v * 4 + 2] = fmaf(-2.f, __uint_as_float(r[slot][c][v * 4 + 2]), n4.z);
-                            w[v * 4 + 3] = fmaf(-2.f, __uint_as_float(r[slot][c][v * 4 + 3]), n4.w);
-                        }
+                        block_scores32(r[slot][c], cn4 + (h + c) * 8, w);
                         int wi;
                         const float m = block_argmin32(w, wi);
                         if (m < best) { // earlier blocks win ties
@@ -682,10 +697,6 @@ __global__ void __launch_bounds__(kThreads, 1)
                         tmem_regs_ready(r[slot ^ 1][1]);
                     }
                 }
-                fence_before_sync();
-                __syncwarp();
-                if (lane == 0)
-                    mbar_arrive_cluster(mapa(smem_u32(&acc_empty[buf]), 0));
             }
             if (abort_flag)
                 break;
