@@ -179,3 +179,25 @@ def test_pair_form_integer_regime_bit_identical(monkeypatch):
     ref = oracle.lloyd_step(x, C)
     assert np.array_equal(lab, ref["labels"])
     assert np.array_equal(cnt, ref["counts"])
+
+
+@pytest.mark.parametrize("pair", ["0", "1"])
+def test_exact_ties_take_the_smallest_centre_index(pair, monkeypatch):
+    """Integer points and centres with exact duplicates placed in the same
+    32-column block, in different blocks of one tile and in different
+    centre tiles (both kernels' tile widths): every label is the smallest
+    index among the tied nearest centres, as in the oracle."""
+    monkeypatch.setenv("KPP_LLOYD_PAIR", pair)
+    N, d, K = 20_000, 24, 700
+    x = datagen.integer_points(N, d, seed=11, n_comp=8)
+    rng = np.random.default_rng(12)
+    C = x[rng.choice(N, K, replace=False)].astype(np.float64)
+    for src, dups in [(3, (17, 40)), (5, (130, 300, 520)), (200, (201, 699)), (257, (0,))]:
+        for j in dups:
+            C[j] = C[src]
+    lab, d2, C2, cnt, phi = _step(x, C)
+    ref = oracle.lloyd_step(x, C)
+    assert np.array_equal(lab, ref["labels"])
+    # the tie rule itself, independently of the oracle
+    D = ((x[:, None, :].astype(np.float64) - C[None, :, :]) ** 2).sum(-1)
+    assert np.array_equal(lab, D.argmin(1))
