@@ -11,6 +11,9 @@
 // product is hi.hi + hi.lo + lo.hi (the dropped lo.lo term is ~2^-16 of the
 // whole).  The epilogue reads the accumulators from tensor memory and keeps
 // the running minimum of |c_k|^2 - 2 x.c_k per point (smallest k on ties).
+// Two kernels compute it: one on pairs of SMs sharing each MMA (cta_group::2,
+// 256 x 256 tiles; the default) and one on single SMs (128 x 128 tiles; where
+// no cluster of two can be launched).
 //
 // The update reads the FP32 points again: the exact squared distance to the
 // assigned centre in the same FP32 difference form as the seeding pass, the

@@ -1,6 +1,8 @@
 // kpp_tc.cuh -- Blackwell (sm_103a) tensor-core plumbing in inline PTX:
 // mbarriers, TMA tile loads, TMEM allocation, tcgen05.mma with shared-memory
-// operand descriptors, and TMEM loads.  Used by the Lloyd assignment kernel.
+// operand descriptors, and TMEM loads, in single-CTA forms and in the forms
+// of a CTA pair sharing its MMAs (cta_group::2).  Used by the Lloyd
+// assignment kernels.
 #pragma once
 
 #include <cuda.h>
