@@ -236,6 +236,10 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(rows)}
 
 
+# GB300 HBM3e bandwidth as specified (the denominators above are measured).
+NOMINAL_HBM_GBS = 8000.0
+
+
 def cpu_info():
     model = None
     try:
@@ -841,8 +845,10 @@ def roofline_for(plan, form_name, N, d, K, eb, has_scales, ms_per_step, wl_name,
          "frac": achieved / peak, "traffic": traffic, "peak_source": src,
          "kernel": f"{form_name}_kernel", "algorithmic_bytes_per_launch": alg_bytes,
          "algorithmic_bytes_per_pass": per_pass, "points_bytes_per_pass": point_bytes,
+         "us_per_pass": 1e3 * per_launch_ms / passes_per_launch,
          "working_set_bytes": working_set, "l2_bytes": l2,
-         "hbm_copy_gbs": hbm_copy, "frac_of_hbm_copy": achieved / hbm_copy}
+         "hbm_copy_gbs": hbm_copy, "frac_of_hbm_copy": achieved / hbm_copy,
+         "nominal_hbm_gbs": NOMINAL_HBM_GBS, "frac_of_nominal_hbm": achieved / NOMINAL_HBM_GBS}
     if "hbm_read_gbs" in peaks_live:
         r["hbm_read_gbs"] = peaks_live["hbm_read_gbs"]
         r["frac_of_hbm_read"] = achieved / peaks_live["hbm_read_gbs"]
@@ -1230,10 +1236,17 @@ def oracle_baseline(stored, scales, K, seed, stream_id, budget_s: float = 15.0):
     t0 = time.perf_counter()
     r = oracle.seed_mt(stored, K_s, seed, stream_id, scales=scales, threads=cores)
     dt = time.perf_counter() - t0
+    import hashlib
+
+    import numpy as np
+
+    # the exact bytes the oracle read (and the GPU path was given)
+    digest = hashlib.sha256(memoryview(np.ascontiguousarray(stored)).cast("B")).hexdigest()
     return {"value": N * K_s * d / dt, "unit": UNIT, "cores": r["threads"], "kind": "oracle",
             "sample": f"full workload data ({N} x {d}), first {K_s} of {K} passes, "
                       f"multi-threaded FP64 oracle on {r['threads']} threads ({dt:.1f} s)",
-            "host_cores": cores, "cpu": model, "seconds": dt}
+            "host_cores": cores, "cpu": model, "seconds": dt,
+            "data_sha256": digest}
 
 
 def main():
