@@ -225,6 +225,13 @@ __device__ __forceinline__ void block_scores32(const uint32_t (&acc)[32], const 
     }
 }
 
+__device__ __forceinline__ uint32_t dynamic_smem_bytes()
+{
+    uint32_t r;
+    asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(r));
+    return r;
+}
+
 __device__ __forceinline__ void fail(Control *ctl, volatile int *abort_flag)
 {
     *abort_flag = 1;
@@ -260,6 +267,15 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint8_t *sA = smem;                              // [buffer][tile][plane][chunk] 16 KB each
     uint8_t *sB = smem + a.abufs * abytes;           // [stage][plane] 16 KB each
     float *s_cn = reinterpret_cast<float *>(sB + NS * 2 * kBBytes);
+    // debug build: the host's plan fits this launch (every thread, before
+    // any barrier or tensor memory is set up)
+    if (!kpp_check(a.ctl,
+                   NS >= 2 && NS <= kMaxStages && (a.abufs == 1 || a.abufs == 2) &&
+                       (size_t)(reinterpret_cast<uint8_t *>(s_cn) - smem_raw) +
+                               (size_t)((K + kBN - 1) / kBN) * kBN * 4 <=
+                           dynamic_smem_bytes(),
+                   501))
+        return;
     __shared__ uint64_t a_full[2], a_empty[2], b_full[kMaxStages], b_empty[kMaxStages], acc_full[2],
         acc_empty[2], done;
     __shared__ uint32_t tmem_base;
@@ -505,6 +521,15 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint8_t *sA = smem;                         // [buffer][plane][chunk] 16 KB each
     uint8_t *sB = smem + a.abufs * abytes;      // [stage][plane] 16 KB each
     float *s_cn = reinterpret_cast<float *>(sB + NS * 2 * kBBytes);
+    // debug build: the host's plan fits this launch (every thread of both
+    // CTAs takes the same branch, before any cluster barrier or allocation)
+    if (!kpp_check(a.ctl,
+                   NS >= 2 && NS <= kMaxStagesPair && (a.abufs == 1 || a.abufs == 2) &&
+                       (size_t)(reinterpret_cast<uint8_t *>(s_cn) - smem_raw) +
+                               (size_t)((K + kPN - 1) / kPN) * kPN * 4 <=
+                           dynamic_smem_bytes(),
+                   502))
+        return;
     __shared__ uint64_t a_full[2], a_empty[2], b_full[kMaxStagesPair], b_empty[kMaxStagesPair],
         acc_full[2], acc_empty[2], done;
     __shared__ uint32_t tmem_base;

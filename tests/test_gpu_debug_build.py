@@ -1,10 +1,12 @@
 """The KPP_DEBUG build of the library (index checks before every hot-path
-memory access of the seeding kernels, a failed check reported as the device
-status KPP_ERR_BOUNDS instead of a memory fault -- the stand-in for a
-sanitizer, which this GPU does not run): the exact-regime parity cases of
-every seeding form run under it, in a child process that loads the debug
-library, and must pass -- every call's status is read, so one index out of
-bounds anywhere fails them."""
+memory access of the seeding kernels, and a check that each tensor-core
+assignment launch's shared-memory plan fits it; a failed check reported as
+the device status KPP_ERR_BOUNDS instead of a memory fault -- the stand-in
+for a sanitizer, which this GPU does not run): the exact-regime parity cases
+of every seeding form, of the Lloyd iteration (both assignment kernels) and
+of k-means|| run under it, in a child process that loads the debug library,
+and must pass -- every call's status is read, so one index out of bounds
+anywhere fails them."""
 import os
 import subprocess
 import sys
@@ -28,6 +30,10 @@ CASES = [
     "tests/test_gpu_batched.py",
     "tests/test_gpu_exact_draws.py::test_exact_decisions_integer_regime",
     "tests/test_gpu_recompute.py",
+    "tests/test_gpu_lloyd.py::test_integer_regime_bit_identical",
+    "tests/test_gpu_lloyd.py::test_pair_form_integer_regime_bit_identical",
+    "tests/test_gpu_lloyd.py::test_exact_ties_take_the_smallest_centre_index",
+    "tests/test_gpu_kmpar.py::test_integer_regime_matches_oracle_exactly",
 ]
 
 
@@ -45,7 +51,7 @@ def test_debug_library_is_the_one_loaded():
     assert out.stdout.strip().endswith(os.path.join("_build_debug", "libkpp.so"))
 
 
-def test_seeding_parity_under_the_debug_build():
+def test_parity_under_the_debug_build():
     r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-m", "gpu", *CASES],
                        capture_output=True, text=True, cwd=ROOT, env=_env(), timeout=1800)
     assert r.returncode == 0, r.stdout[-4000:] + r.stderr[-2000:]
