@@ -1038,7 +1038,9 @@ def run_seeding(args, rank, world, local, dev, pg, barrier):
                      "gpu_launches": fr["plan"]["launches"] * fr["steps"],
                      "roofline": {k: froof[k] for k in
                                   ("bound", "achieved", "peak", "frac", "traffic",
-                                   "frac_of_hbm_read", "algorithmic_bytes_per_pass")
+                                   "traffic_over_algorithmic", "frac_of_hbm_read",
+                                   "frac_of_nominal_hbm", "us_per_pass",
+                                   "algorithmic_bytes_per_pass")
                                   if k in froof}}
             if not args.no_phi:
                 entry["phi"] = phi_gate(fd, fr)
