@@ -275,3 +275,31 @@ def test_full_size_workload_parity(form):
     st, sc, idx, d2, phi = run(x, wl.K, seed=wl.draw_seed, opts={"form": form})
     events = parity.check(st, wl.K, wl.draw_seed, 0, idx, d2, phi)
     assert events <= 2
+
+
+def test_random_shapes_sweep():
+    """Seeded random shapes in the exact (integer) regime: N log-uniform in
+    [1, 200 000], d from specialised and generic widths, K up to 300, random
+    draw seed and stream, random CTA block sizes; per shape two random
+    (form, storage) pairs among auto / streamed / persistent / small and
+    FP32 / BF16, each bit-identical to the oracle (a form that cannot take
+    the shape must say so with KPP_ERR_UNSUPPORTED)."""
+    rng = np.random.default_rng(7)
+    dims = [1, 2, 3, 4, 5, 7, 8, 16, 17, 32, 33, 64, 100, 128]
+    forms = [kpp.FORM_AUTO, STREAMED, PERSISTENT, kpp.FORM_SMALL]
+    for case in range(24):
+        N = int(round(np.exp(rng.uniform(0.0, np.log(200_000)))))
+        d = int(rng.choice(dims))
+        K = int(rng.integers(1, min(N, 300) + 1))
+        seed, sid = int(rng.integers(1, 1 << 30)), int(rng.integers(0, 1000))
+        x = datagen.integer_points(N, d, seed=case, n_comp=int(rng.integers(1, 9)))
+        for _ in range(2):
+            form = int(rng.choice(forms))
+            dtype = str(rng.choice(["f32", "bf16"]))
+            opts = {"form": form, "min_rows_per_cta": int(rng.choice([0, 128, 1024]))}
+            try:
+                st, sc, idx, d2, phi = run(x, K, seed=seed, stream_id=sid, dtype=dtype, opts=opts)
+            except kpp.KppError as e:
+                assert e.status == kpp.ERR_UNSUPPORTED and form != kpp.FORM_AUTO, (N, d, K, form)
+                continue
+            parity.check(st, K, seed, sid, idx, d2, phi, scales=sc, exact=True)
